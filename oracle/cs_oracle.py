@@ -1,0 +1,385 @@
+"""FP64 CPU oracle for circulant LASSO recovery (arXiv 1707.02244).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import or call
+this module.  The product path (the CUDA library and its Python binding) never
+does, and this module never imports the product package: the two share no
+code.  Inputs arrive as plain arrays (the seeded generators live in ``synth``).
+
+Everything here is plain numpy in float64.  Each function follows one passage
+of the paper, cited as section / equation / algorithm:
+
+* dense oracle: the sensing matrix is built explicitly and every product is a
+  dense mat-vec; ADMM's x-update solve uses a dense Cholesky factor;
+* FFT oracle: the same algorithms with the circulant products taken through
+  numpy's FFT (a library primitive used as one step), for sizes where dense
+  matrices do not fit.  It is pinned against the dense oracle by the tests.
+
+Conventions (readings of the paper, all listed in the design notes):
+
+* circulant index (Sec. 4.2): ``C[i, j] = c[(j - i) mod n]``; ``c`` is the
+  first row of C;
+* A = P C (Sec. 4.3): P keeps the rows ``rows`` of C; ``y[i]`` pairs with row
+  ``rows[i]``; ``P^T y`` is y zero-filled onto those rows;
+* LASSO (Eq. 3) is minimised in the equivalent form
+  ``0.5 ||y - A x||^2 + lam ||x||_1`` (lam plays the role of alpha);
+* ISTA (Algorithm 1) thresholds at ``tau * lam`` (proximal-gradient reading);
+* soft threshold (Eq. 4): ``|x| == gamma`` maps to 0.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+__all__ = [
+    "circulant_matrix", "sensing_matrix", "soft_threshold", "lasso_objective",
+    "kkt_violation", "forward_dense", "adjoint_dense", "spectrum",
+    "forward_fft", "adjoint_fft", "circulant_apply_fft", "ista_dense",
+    "ista_fft", "admm_dense", "admm_fft", "admm_standard_dense",
+    "admm_d_diagonal", "opnorm2_dense", "opnorm2_power_fft",
+    "lasso_bruteforce", "l0_bruteforce", "nmse", "naive_dft",
+]
+
+
+# --------------------------------------------------------------------------
+# Sensing operator (Sec. 4.2, Sec. 4.3)
+# --------------------------------------------------------------------------
+
+def circulant_matrix(c: np.ndarray) -> np.ndarray:
+    """Dense circulant C with ``C[i, j] = c[(j - i) mod n]`` (Sec. 4.2).
+
+    Each row is the previous row shifted circularly one place to the right.
+    """
+    c = np.asarray(c, dtype=np.float64)
+    n = c.shape[0]
+    i = np.arange(n)[:, None]
+    j = np.arange(n)[None, :]
+    return c[(j - i) % n]
+
+
+def sensing_matrix(c: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """Partial circulant A = P C: the rows ``rows`` of C, in the given order
+    (Sec. 4.3, P selects the rows in Omega)."""
+    return circulant_matrix(c)[np.asarray(rows, dtype=np.int64), :]
+
+
+def forward_dense(c, rows, x):
+    """A x by dense mat-vec (Algorithm 1, residual step)."""
+    return sensing_matrix(c, rows) @ np.asarray(x, dtype=np.float64)
+
+
+def adjoint_dense(c, rows, r):
+    """A^T r by dense mat-vec (Algorithm 1, gradient step)."""
+    return sensing_matrix(c, rows).T @ np.asarray(r, dtype=np.float64)
+
+
+def naive_dft(v: np.ndarray) -> np.ndarray:
+    """O(n^2) DFT ``V_k = sum_j v_j exp(-2 pi i j k / n)`` (no FFT library)."""
+    v = np.asarray(v, dtype=np.complex128)
+    n = v.shape[0]
+    jk = np.outer(np.arange(n), np.arange(n)) % n
+    return np.exp(-2j * np.pi * jk / n) @ v
+
+
+def spectrum(c: np.ndarray) -> np.ndarray:
+    """DFT of the generating vector, ``chat = FFT(c)`` (Sec. 4.2: circulant
+    matrices are diagonalised by the Fourier matrix)."""
+    return np.fft.fft(np.asarray(c, dtype=np.float64))
+
+
+def circulant_apply_fft(chat: np.ndarray, x: np.ndarray, transpose: bool = False):
+    """C x (or C^T x) through the convolution theorem.
+
+    With ``C[i, j] = c[(j - i) mod n]`` and real c, ``FFT(C x) = conj(chat) *
+    FFT(x)`` and ``FFT(C^T x) = chat * FFT(x)``.
+    """
+    xh = np.fft.fft(np.asarray(x, dtype=np.float64))
+    h = chat if transpose else np.conj(chat)
+    return np.fft.ifft(h * xh).real
+
+
+def forward_fft(chat, rows, x):
+    """A x = (C x)[rows] (Sec. 4.3) with C x taken by FFT."""
+    return circulant_apply_fft(chat, x)[np.asarray(rows, dtype=np.int64)]
+
+
+def zero_fill(n: int, rows, r):
+    """P^T r: r scattered onto the rows of Omega, zero elsewhere (Sec. 4.3)."""
+    out = np.zeros(n, dtype=np.float64)
+    out[np.asarray(rows, dtype=np.int64)] = np.asarray(r, dtype=np.float64)
+    return out
+
+
+def adjoint_fft(chat, rows, r):
+    """A^T r = C^T P^T r (Sec. 4.3) with C^T taken by FFT."""
+    n = chat.shape[0]
+    return circulant_apply_fft(chat, zero_fill(n, rows, r), transpose=True)
+
+
+# --------------------------------------------------------------------------
+# LASSO pieces (Eq. 3, Eq. 4)
+# --------------------------------------------------------------------------
+
+def soft_threshold(x, gamma):
+    """Eq. 4: ``sgn(x)(|x| - gamma)`` where ``|x| > gamma``, else 0."""
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(np.abs(x) > gamma, np.sign(x) * (np.abs(x) - gamma), 0.0)
+
+
+def lasso_objective(A, y, x, lam):
+    """``0.5 ||y - A x||^2 + lam ||x||_1`` -- Eq. 3 divided by 2 (same
+    minimiser, lam = alpha; the split form of Sec. 4.3 uses this scaling)."""
+    r = y - A @ x
+    return 0.5 * float(r @ r) + lam * float(np.abs(x).sum())
+
+
+def kkt_violation(A, y, x, lam):
+    """Largest violation of the LASSO optimality conditions at x.
+
+    With ``g = A^T (y - A x)``: on the support ``g_i = lam sgn(x_i)``; off the
+    support ``|g_i| <= lam``.  Returns the max violation (0 at a minimiser).
+    """
+    g = A.T @ (y - A @ x)
+    on = x != 0
+    v_on = np.abs(g[on] - lam * np.sign(x[on])).max(initial=0.0)
+    v_off = np.maximum(np.abs(g[~on]) - lam, 0.0).max(initial=0.0)
+    return max(v_on, v_off)
+
+
+def nmse(x, x_true):
+    """Normalised MSE ``||x - x*||^2 / ||x*||^2`` (the MSE of Sec. 6 divided
+    by the signal energy per sample)."""
+    x = np.asarray(x, dtype=np.float64)
+    x_true = np.asarray(x_true, dtype=np.float64)
+    d = x - x_true
+    return float(d @ d) / float(x_true @ x_true)
+
+
+# --------------------------------------------------------------------------
+# ISTA (Algorithm 1)
+# --------------------------------------------------------------------------
+
+def _ista(apply_A, apply_At, y, lam, tau, iters, x0, n, history):
+    x = np.zeros(n) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
+    hist = [x.copy()] if history else None
+    for _ in range(iters):
+        r = y - apply_A(x)                  # residual r(t) = y - A x(t-1)
+        delta = tau * apply_At(r)           # gradient step tau A^T r(t)
+        x = soft_threshold(x + delta, tau * lam)   # x(t) = eta[x(t-1) + delta]
+        if history:
+            hist.append(x.copy())
+    return (x, hist) if history else x
+
+
+def ista_dense(c, rows, y, lam, tau, iters, x0=None, history=False):
+    """Algorithm 1 with a dense A = P C.  Threshold ``tau * lam``."""
+    A = sensing_matrix(c, rows)
+    y = np.asarray(y, dtype=np.float64)
+    return _ista(lambda v: A @ v, lambda r: A.T @ r, y, lam, tau, iters, x0,
+                 A.shape[1], history)
+
+
+def ista_fft(c, rows, y, lam, tau, iters, x0=None, history=False):
+    """Algorithm 1 with A x and A^T r taken by FFT (same steps as ista_dense)."""
+    chat = spectrum(c)
+    y = np.asarray(y, dtype=np.float64)
+    return _ista(lambda v: forward_fft(chat, rows, v),
+                 lambda r: adjoint_fft(chat, rows, r), y, lam, tau, iters, x0,
+                 chat.shape[0], history)
+
+
+# --------------------------------------------------------------------------
+# Circulant ADMM (Algorithm 3)
+# --------------------------------------------------------------------------
+
+def admm_d_diagonal(n, rows, rho):
+    """Diagonal of D = (P^T P + rho I)^(-1) (Algorithm 3, initial inversion).
+
+    P^T P is diagonal with 1 on Omega and 0 elsewhere, so D is ``1/(1+rho)``
+    on Omega and ``1/rho`` elsewhere (Sec. 4.3)."""
+    d = np.full(n, 1.0 / rho)
+    d[np.asarray(rows, dtype=np.int64)] = 1.0 / (1.0 + rho)
+    return d
+
+
+def _admm(C_apply, Ct_apply, B_apply, n, rows, y, lam, sigma, rho, tau1, tau2,
+          iters, state, history):
+    d = admm_d_diagonal(n, rows, rho)
+    pty = zero_fill(n, rows, y)
+    if state is None:
+        v = np.zeros(n); z = np.zeros(n); mu = np.zeros(n); nu = np.zeros(n)
+    else:
+        v, z, mu, nu = (np.asarray(s, dtype=np.float64).copy() for s in state)
+    x = np.zeros(n)
+    hist = [] if history else None
+    for _ in range(iters):
+        # primal update (Algorithm 3): x then v
+        x = B_apply(rho * Ct_apply(v) + sigma * (z - nu))
+        cx = C_apply(x)
+        v = d * (rho * cx - rho * mu + pty)
+        # soft-thresholding step
+        z = soft_threshold(x + nu, lam / sigma)
+        # dual update, then v <- v + mu
+        mu = mu + tau1 * (v - cx)
+        nu = nu + tau2 * (x - z)
+        v = v + mu
+        if history:
+            hist.append((x.copy(), z.copy()))
+    out = {"x": x, "z": z, "mu": mu, "nu": nu, "v": v}
+    if history:
+        out["history"] = hist
+    return out
+
+
+def admm_dense(c, rows, y, lam, sigma, rho, tau1=1.0, tau2=1.0, iters=100,
+               state=None, history=False):
+    """Algorithm 3 with dense C; B = (rho C^T C + sigma I)^(-1) applied by a
+    dense Cholesky factor computed once (the "initial inversion").
+
+    ``state`` = (v, z, mu, nu) to warm-start (v is the folded v + mu of the
+    last line of the loop); ``None`` is the paper's zero start.
+    Returns dict with x, z, mu, nu, v after ``iters`` iterations.
+    """
+    C = circulant_matrix(c)
+    n = C.shape[0]
+    M = rho * (C.T @ C) + sigma * np.eye(n)
+    L = np.linalg.cholesky(M)
+
+    def B_apply(b):
+        return np.linalg.solve(L.T, np.linalg.solve(L, b))
+
+    return _admm(lambda v: C @ v, lambda v: C.T @ v, B_apply, n, rows,
+                 np.asarray(y, dtype=np.float64), lam, sigma, rho, tau1, tau2,
+                 iters, state, history)
+
+
+def admm_fft(c, rows, y, lam, sigma, rho, tau1=1.0, tau2=1.0, iters=100,
+             state=None, history=False):
+    """Algorithm 3 with the circulant inverse taken by FFT (Sec. 4.3: rho C^T C
+    + sigma I is circulant with eigenvalues ``rho |chat|^2 + sigma``)."""
+    chat = spectrum(c)
+    n = chat.shape[0]
+    bhat = 1.0 / (rho * np.abs(chat) ** 2 + sigma)
+
+    def B_apply(b):
+        return np.fft.ifft(bhat * np.fft.fft(b)).real
+
+    return _admm(lambda v: circulant_apply_fft(chat, v),
+                 lambda v: circulant_apply_fft(chat, v, transpose=True),
+                 B_apply, n, rows, np.asarray(y, dtype=np.float64), lam, sigma,
+                 rho, tau1, tau2, iters, state, history)
+
+
+def admm_standard_dense(A, y, lam, rho, iters):
+    """Algorithm 2 (standard ADMM) with B = (A^T A + rho I)^(-1) by Cholesky.
+
+    Cross-check only: it minimises the same LASSO as Algorithm 3 with the
+    threshold ``lam / rho``.  Returns (x, z, u)."""
+    A = np.asarray(A, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    n = A.shape[1]
+    L = np.linalg.cholesky(A.T @ A + rho * np.eye(n))
+    aty = A.T @ y
+    x = np.zeros(n); z = np.zeros(n); u = np.zeros(n)
+    for _ in range(iters):
+        b = aty + rho * (z - u)
+        x = np.linalg.solve(L.T, np.linalg.solve(L, b))
+        z = soft_threshold(x + u, lam / rho)
+        u = u + x - z
+    return x, z, u
+
+
+# --------------------------------------------------------------------------
+# Step size (Algorithm 1 initialisation: tau in (0, ||A||^-2))
+# --------------------------------------------------------------------------
+
+def opnorm2_dense(c, rows):
+    """||A||_2^2 from the SVD of the dense A."""
+    s = np.linalg.svd(sensing_matrix(c, rows), compute_uv=False)
+    return float(s[0] ** 2)
+
+
+def opnorm2_power_fft(c, rows, iters=200, seed=0, tol=1e-12):
+    """||A||_2^2 by power iteration on A^T A with FFT products."""
+    chat = spectrum(c)
+    n = chat.shape[0]
+    u = np.random.default_rng(seed).standard_normal(n)
+    u /= np.linalg.norm(u)
+    lam_prev = 0.0
+    lam_est = 0.0
+    for _ in range(iters):
+        w = adjoint_fft(chat, rows, forward_fft(chat, rows, u))
+        lam_est = float(u @ w)
+        u = w / np.linalg.norm(w)
+        if abs(lam_est - lam_prev) <= tol * abs(lam_est):
+            break
+        lam_prev = lam_est
+    return lam_est
+
+
+# --------------------------------------------------------------------------
+# Brute force on tiny instances (Eq. 2, Eq. 3)
+# --------------------------------------------------------------------------
+
+def lasso_bruteforce(A, y, lam):
+    """Exact LASSO minimiser by enumerating sign patterns (n <= ~10).
+
+    For a sign pattern s with support S the optimality conditions give
+    ``x_S = (A_S^T A_S)^(-1) (A_S^T y - lam s_S)``; the pattern is accepted when
+    sgn(x_S) = s_S and ``|A_j^T (y - A x)| <= lam`` off S.  Among accepted
+    patterns the one with the smallest objective is returned.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    n = A.shape[1]
+    best = None
+    best_f = np.inf
+    for s in itertools.product((-1, 0, 1), repeat=n):
+        s = np.array(s, dtype=np.float64)
+        S = np.flatnonzero(s)
+        x = np.zeros(n)
+        if S.size:
+            As = A[:, S]
+            G = As.T @ As
+            if np.linalg.matrix_rank(G) < S.size:
+                continue
+            xs = np.linalg.solve(G, As.T @ y - lam * s[S])
+            if np.any(np.sign(xs) != s[S]):
+                continue
+            x[S] = xs
+        g = A.T @ (y - A @ x)
+        off = np.setdiff1d(np.arange(n), S)
+        if off.size and np.any(np.abs(g[off]) > lam * (1 + 1e-12)):
+            continue
+        f = lasso_objective(A, y, x, lam)
+        if f < best_f:
+            best_f = f
+            best = x
+    return best
+
+
+def l0_bruteforce(A, y, kmax, tol=1e-9):
+    """Sparsest x with A x = y among supports of size <= kmax (Eq. 2).
+
+    Returns (x, list_of_supports_of_that_size_that_fit)."""
+    A = np.asarray(A, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    n = A.shape[1]
+    scale = max(1.0, float(np.linalg.norm(y)))
+    if np.linalg.norm(y) <= tol:
+        return np.zeros(n), [()]
+    for k in range(1, kmax + 1):
+        fits = []
+        xbest = None
+        for S in itertools.combinations(range(n), k):
+            As = A[:, S]
+            xs, *_ = np.linalg.lstsq(As, y, rcond=None)
+            if np.linalg.norm(As @ xs - y) <= tol * scale:
+                fits.append(S)
+                if xbest is None:
+                    xbest = np.zeros(n)
+                    xbest[list(S)] = xs
+        if fits:
+            return xbest, fits
+    return None, []

@@ -1,0 +1,113 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module draws random numbers only: generating vectors, row sets, sparse
+signals and noise.  It holds none of the method's arithmetic (no products with
+the sensing matrix, no thresholds, no FFTs); measurements y = A x* are formed
+by whichever side consumes the inputs.  Both the oracle's tests and the GPU
+tests / bench draw from here, so they see identical numbers.
+
+Workloads (Sec. 6 shapes, with the readings recorded in the design notes):
+
+* ``small_instance``: n=4096, m=1024 rows without replacement, c ~ N(0, 1/m),
+  x* with exactly k=64 nonzeros on a uniform support, N(0,1) amplitudes,
+  noiseless;
+* ``large_instance``: n=2^22, m=n/4, c ~ N(0, 1/m), x* Bernoulli(1/200)
+  support with N(0,1) amplitudes, noise N(0, 1e-4^2).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+SMALL_SEED = 1707000
+LARGE_SEED = 1707001
+
+
+@dataclass
+class Instance:
+    n: int
+    m: int
+    c: np.ndarray        # float64 [n]: first row of the circulant C
+    rows: np.ndarray     # int64 [m]: distinct rows of C kept by P, in draw order
+    x_true: np.ndarray   # float64 [n]: sparse signal x*
+    noise: np.ndarray    # float64 [m]: additive measurement noise (may be zeros)
+    seed: int
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def draw_rows(g: np.random.Generator, n: int, m: int) -> np.ndarray:
+    """m distinct rows of {0..n-1}, uniformly without replacement, in draw
+    order (not sorted)."""
+    return g.choice(n, size=m, replace=False).astype(np.int64)
+
+
+def gaussian_c(g: np.random.Generator, n: int, m: int) -> np.ndarray:
+    """Generating vector with i.i.d. N(0, 1/m) entries."""
+    return g.standard_normal(n) / np.sqrt(m)
+
+
+def k_sparse(g: np.random.Generator, n: int, k: int) -> np.ndarray:
+    """Exactly k nonzeros on a uniform random support, N(0,1) amplitudes."""
+    x = np.zeros(n)
+    supp = g.choice(n, size=k, replace=False)
+    x[supp] = g.standard_normal(k)
+    return x
+
+
+def bernoulli_gaussian(g: np.random.Generator, n: int, p: float) -> np.ndarray:
+    """Each entry nonzero with probability p, N(0,1) amplitude."""
+    on = g.random(n) < p
+    return np.where(on, g.standard_normal(n), 0.0)
+
+
+def instance(n: int, m: int, *, k: int | None = None, p: float | None = None,
+             noise_std: float = 0.0, seed: int = 0) -> Instance:
+    """Generic seeded instance: c ~ N(0,1/m), rows, x* (k-sparse or
+    Bernoulli(p)-Gaussian), noise N(0, noise_std^2)."""
+    g = rng(seed)
+    c = gaussian_c(g, n, m)
+    rows = draw_rows(g, n, m)
+    if k is not None:
+        x = k_sparse(g, n, k)
+    elif p is not None:
+        x = bernoulli_gaussian(g, n, p)
+    else:
+        x = np.zeros(n)
+    noise = g.standard_normal(m) * noise_std if noise_std > 0 else np.zeros(m)
+    return Instance(n, m, c, rows, x, noise, seed)
+
+
+def small_instance(seed: int = SMALL_SEED) -> Instance:
+    """n=4096, m=1024, k=64, noiseless (lambda=1e-3, 500 iterations)."""
+    return instance(4096, 1024, k=64, seed=seed)
+
+
+def large_instance(seed: int = LARGE_SEED, n: int = 1 << 22) -> Instance:
+    """n=2^22, m=n/4, Bernoulli(1/200)-Gaussian x*, noise N(0,1e-4^2)
+    (lambda=5e-3, rho=1, stop at NMSE<=1e-4 or 2000 iterations)."""
+    return instance(n, n // 4, p=1.0 / 200.0, noise_std=1e-4, seed=seed)
+
+
+def random_vector(n: int, seed: int) -> np.ndarray:
+    """Dense N(0,1) vector (operator tests)."""
+    return rng(seed).standard_normal(n)
+
+
+def unit_modulus_c(n: int, seed: int) -> np.ndarray:
+    """Random phases for a real generating vector whose circulant is
+    orthogonal: returns the spectrum samples (complex, Hermitian, |.|=1)
+    as an array of length n.  The consumer turns it into c by an inverse DFT.
+    """
+    g = rng(seed)
+    ph = g.uniform(0.0, 2.0 * np.pi, size=n)
+    spec = np.exp(1j * ph)
+    spec[0] = 1.0 if g.random() < 0.5 else -1.0
+    if n % 2 == 0:
+        spec[n // 2] = 1.0 if g.random() < 0.5 else -1.0
+    k = np.arange(1, (n + 1) // 2)
+    spec[n - k] = np.conj(spec[k])
+    return spec

@@ -1,0 +1,117 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that the
+pins catch every one of them: a transposed operand, a wrong index, a dropped
+term, a flipped sign, a wrong threshold."""
+import numpy as np
+import pytest
+
+import oracle.cs_oracle as O
+from oracle_pins import ALL_CHECKS
+
+
+def _mut_transposed_circulant(c):
+    c = np.asarray(c, dtype=np.float64)
+    n = c.shape[0]
+    i = np.arange(n)[:, None]
+    j = np.arange(n)[None, :]
+    return c[(i - j) % n]
+
+
+def _mut_reverse_circulant(c):
+    # the i + j indexing of the ISTA kernels printed in Sec. 5.2
+    c = np.asarray(c, dtype=np.float64)
+    n = c.shape[0]
+    i = np.arange(n)[:, None]
+    j = np.arange(n)[None, :]
+    return c[(i + j) % n]
+
+
+def _mut_conj_fft(chat, x, transpose=False):
+    xh = np.fft.fft(np.asarray(x, dtype=np.float64))
+    h = np.conj(chat) if transpose else chat
+    return np.fft.ifft(h * xh).real
+
+
+def _mut_threshold_hard(x, gamma):
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(np.abs(x) > gamma, x, 0.0)
+
+
+def _mut_d_minus(n, rows, rho):
+    d = np.full(n, 1.0 / rho)
+    d[np.asarray(rows, dtype=np.int64)] = 1.0 / (1.0 - rho) if rho != 1.0 else 0.5
+    return d
+
+
+def _mut_ista_threshold_lam(apply_A, apply_At, y, lam, tau, iters, x0, n, history):
+    x = np.zeros(n) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
+    hist = [x.copy()] if history else None
+    for _ in range(iters):
+        r = y - apply_A(x)
+        x = O.soft_threshold(x + tau * apply_At(r), lam)
+        if history:
+            hist.append(x.copy())
+    return (x, hist) if history else x
+
+
+def _mut_ista_residual_sign(apply_A, apply_At, y, lam, tau, iters, x0, n, history):
+    x = np.zeros(n) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
+    hist = [x.copy()] if history else None
+    for _ in range(iters):
+        r = apply_A(x) - y
+        x = O.soft_threshold(x + tau * apply_At(r), tau * lam)
+        if history:
+            hist.append(x.copy())
+    return (x, hist) if history else x
+
+
+def _admm_variant(drop_sigma=False, no_fold=False, nu_sign=+1, z_thr_rho=False):
+    def _admm(C_apply, Ct_apply, B_apply, n, rows, y, lam, sigma, rho, tau1,
+              tau2, iters, state, history):
+        d = O.admm_d_diagonal(n, rows, rho)
+        pty = O.zero_fill(n, rows, y)
+        if state is None:
+            v = np.zeros(n); z = np.zeros(n); mu = np.zeros(n); nu = np.zeros(n)
+        else:
+            v, z, mu, nu = (np.asarray(s, dtype=np.float64).copy() for s in state)
+        x = np.zeros(n)
+        for _ in range(iters):
+            s = 1.0 if drop_sigma else sigma
+            x = B_apply(rho * Ct_apply(v) + s * (z - nu))
+            cx = C_apply(x)
+            v = d * (rho * cx - rho * mu + pty)
+            z = O.soft_threshold(x + nu, lam / (rho if z_thr_rho else sigma))
+            mu = mu + tau1 * (v - cx)
+            nu = nu + nu_sign * tau2 * (x - z)
+            if not no_fold:
+                v = v + mu
+        return {"x": x, "z": z, "mu": mu, "nu": nu, "v": v}
+    return _admm
+
+
+MUTANTS = {
+    "transposed_circulant": ("circulant_matrix", _mut_transposed_circulant),
+    "reverse_circulant": ("circulant_matrix", _mut_reverse_circulant),
+    "fft_conj_swapped": ("circulant_apply_fft", _mut_conj_fft),
+    "hard_threshold": ("soft_threshold", _mut_threshold_hard),
+    "d_minus_rho": ("admm_d_diagonal", _mut_d_minus),
+    "ista_threshold_lam": ("_ista", _mut_ista_threshold_lam),
+    "ista_residual_sign": ("_ista", _mut_ista_residual_sign),
+    "admm_drop_sigma": ("_admm", _admm_variant(drop_sigma=True)),
+    "admm_no_fold": ("_admm", _admm_variant(no_fold=True)),
+    "admm_nu_sign": ("_admm", _admm_variant(nu_sign=-1)),
+    "admm_threshold_rho": ("_admm", _admm_variant(z_thr_rho=True)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, monkeypatch):
+    attr, fn = MUTANTS[name]
+    monkeypatch.setattr(O, attr, fn)
+    caught = []
+    for check in ALL_CHECKS:
+        try:
+            with np.errstate(all="ignore"):
+                check(O)
+        except (AssertionError, np.linalg.LinAlgError, ValueError, ZeroDivisionError):
+            caught.append(check.__name__)
+    assert caught, f"mutant {name} passed every pin"

@@ -1,0 +1,422 @@
+"""Throughput of the circulant ISTA / ADMM hot path on GB300.
+
+Workload (one "step"): on the n = 2^22, m = n/4 instance (c ~ N(0, 1/m),
+Bernoulli(1/200)-Gaussian x*, noise N(0, 1e-4^2), lambda = 5e-3):
+  ISTA (Algorithm 1) for T iterations from x = 0, tau = 1 / ||A||^2 (GPU power
+  iteration), then ADMM (Algorithm 3, sigma = rho = 1, tau1 = tau2 = 1) for T
+  iterations from the zero state; stopping norms (NMSE, relative change,
+  objective) are formed on the device every 10 iterations.
+value = iterations (ISTA + ADMM) per second over the whole job.
+
+Inputs are resident in HBM when a step starts; L2 is flushed (a 512 MiB
+write) between steps, outside the timed events.  Plan construction (FP64
+spectrum, tables) and the power iteration are set-up, reported separately.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--iters T] [--impl reference]
+
+Under torchrun each rank solves its own instance (replicas, no collective on
+the data path) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import pathlib
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = pathlib.Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+import synth  # noqa: E402
+
+LAM = 5e-3
+RHO = 1.0
+METRIC = "ISTA/ADMM iter/s and time-to-NMSE 1e-4 at n=2^22; fraction of HBM roofline"
+WORKLOAD = "1D ISTA+ADMM, n=2^22, m=n/4, c~N(0,1/m), x* Bernoulli(1/200)-Gaussian, noise 1e-4, lambda=5e-3, rho=1"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--iters", type=int, default=200, help="ISTA and ADMM iterations per step")
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 22)
+    ap.add_argument("--no-extras", action="store_true", help="skip time-to-NMSE, roofline and CPU legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- CPU legs
+
+def oracle_sample(inst, iters_each):
+    """Time the FP64 oracle (as it stands) on the host: iters_each ISTA and
+    iters_each ADMM iterations of the same workload.  Returns (seconds, its)."""
+    import oracle.cs_oracle as O
+    chat = O.spectrum(inst.c)
+    y = O.forward_fft(chat, inst.rows, inst.x_true) + inst.noise
+    tau = 1.0 / float(np.max(np.abs(chat) ** 2))
+    t0 = time.perf_counter()
+    O.ista_fft(inst.c, inst.rows, y, LAM, tau, iters_each)
+    O.admm_fft(inst.c, inst.rows, y, LAM, sigma=RHO, rho=RHO, iters=iters_each)
+    return time.perf_counter() - t0, 2 * iters_each
+
+
+def cpu_baseline(inst):
+    secs, its = oracle_sample(inst, 6)
+    return {"value": its / secs, "unit": "iter/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, {its // 2} ISTA + {its // 2} ADMM iterations at n=2^22 "
+                      f"({secs:.1f} s; numpy FFT runs on one thread)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    inst = synth.large_instance(n=args.n)
+    per = 1
+    for _ in range(args.warmup):
+        oracle_sample(inst, per)
+    times = []
+    for _ in range(args.steps):
+        secs, its = oracle_sample(inst, per)
+        times.append(secs)
+    total = sum(times)
+    value = 2 * per * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": inst.n, "m": inst.m,
+                   "step": f"{per} ISTA + {per} ADMM iterations (bounded sample of the GPU step)"},
+        "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per} ISTA + {per} ADMM FP64 oracle iterations per step"},
+        "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = ROOT / "gpurun_out" / f"clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.path.parent.mkdir(exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.path.read_text().splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        try:
+            self.path.unlink()
+        except Exception:
+            pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+PASS_NAMES = {0: "mid_kernel<MID_FWD>", 1: "col_kernel<COL_RESIDUAL>", 2: "mid_kernel<MID_ADJ>",
+              3: "col_kernel<COL_ISTA>", 4: "mid_kernel<MID_ADMM>", 5: "col_kernel<COL_ADMM>"}
+
+
+def pass_bytes(pid, n, m):
+    """Algorithmic bytes of one launch of each pass (compulsory reads and
+    writes of the exchange buffer, tables, state and measurements)."""
+    N = n // 2
+    if pid in (0, 2):            # real-FFT mid pass: W in/out + (P, Q) table
+        return 16 * N + 16 * (N // 2)
+    if pid == 1:                 # residual column pass: W in/out + y + mask + prefix
+        return 16 * N + 4 * m + n // 8 + n // 8
+    if pid == 3:                 # ISTA update column pass: W in/out + x in/out
+        return 16 * N + 8 * n
+    if pid == 4:                 # ADMM mid pass: W in/out (complex n) + chat + bhat
+        return 16 * n + 8 * (n // 2) + 4 * (n // 2)
+    return 16 * n + 16 * n + 4 * m + n // 4   # ADMM column pass: W, mu, nu in/out, y, mask
+
+
+def traffic_record(pid):
+    """ncu DRAM bytes per launch from profiles/dram_traffic.txt, valid only
+    while the kernel sources are unchanged."""
+    f = ROOT / "profiles" / "dram_traffic.txt"
+    if not f.exists():
+        return None
+    src = hashlib.sha256()
+    for p in sorted((ROOT / "paper_1707_02244_gb300" / "csrc").glob("*")):
+        src.update(p.read_bytes())
+    digest = src.hexdigest()[:16]
+    for ln in f.read_text().splitlines():
+        parts = ln.split()
+        if len(parts) >= 4 and parts[0] == "pass" and parts[1] == str(pid) and parts[3] == digest:
+            return float(parts[2])
+    return None
+
+
+def run_gpu(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_1707_02244_gb300 as cs
+
+    stream = torch.cuda.current_stream(dev)
+    inst = synth.large_instance(seed=synth.LARGE_SEED + rank, n=args.n)
+    n, m, T = inst.n, inst.m, args.iters
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = cs.cs_plan(n, m, inst.rows, inst.c, stream)
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+
+    xt = torch.from_numpy(inst.x_true.astype(np.float32)).to(dev)
+    y = torch.empty(m, dtype=torch.float32, device=dev)
+    cs.cs_forward(plan, xt, y)
+    y += torch.from_numpy(inst.noise.astype(np.float32)).to(dev)
+    t0 = time.perf_counter()
+    L = cs.cs_opnorm2(plan, 100)
+    opnorm_ms = 1e3 * (time.perf_counter() - t0)
+    tau = float(np.float32(1.0 / L))
+    x = torch.zeros(n, dtype=torch.float32, device=dev)
+    z = torch.zeros(n, dtype=torch.float32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        x.zero_()
+        cs.cs_ista(plan, y, LAM, tau, T, x, stats=False)
+        cs.cs_admm(plan, y, LAM, RHO, T, z, stats=False)
+
+    # kernels per step, from the library's own count
+    st_i = cs.cs_ista(plan, y, LAM, tau, T, x)
+    st_a = cs.cs_admm(plan, y, LAM, RHO, T, z)
+    launches_per_step = st_i["launches"] + st_a["launches"]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * 2 * T * args.steps / total_s
+
+    # e2e through the public API: pinned host y in, x and z out, every step
+    y_h = torch.empty(m, dtype=torch.float32, pin_memory=True)
+    y_h.copy_(y.cpu())
+    x_h = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    z_h = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    y_in = torch.empty_like(y)
+    e2e_steps = max(3, args.steps // 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        y_in.copy_(y_h, non_blocking=True)
+        x.zero_()
+        cs.cs_ista(plan, y_in, LAM, tau, T, x, stats=False)
+        cs.cs_admm(plan, y_in, LAM, RHO, T, z, stats=False)
+        x_h.copy_(x, non_blocking=True)
+        z_h.copy_(z, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    e2e_value = world * 2 * T * e2e_steps / e2e_s
+
+    extras = {}
+    roof = None
+    if not args.no_extras and rank == 0:
+        roof, extras["passes"] = measure_passes(cs, plan, y, x, z, tau, n, m, flush, stream, torch)
+        extras["time_to_nmse_1e-4"] = time_to_nmse(cs, plan, y, xt, tau, n, dev, torch)
+    cs.cs_set_monitor(plan, None, 0.0, 10)
+
+    # ISTA and ADMM iteration rates on their own (same buffers, warm L2)
+    sep = {}
+    for name, fn in (("ista", lambda: cs.cs_ista(plan, y, LAM, tau, T, x, stats=False)),
+                     ("admm", lambda: cs.cs_admm(plan, y, LAM, RHO, T, z, stats=False))):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(5):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        sep[name] = 5 * T / (a.elapsed_time(b) / 1e3)
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_extras:
+            cpu = cpu_baseline(inst)
+        line = {
+            "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "m": m, "iters_per_solver_per_step": T,
+                       "l2": "flushed (512 MiB write) between steps, outside the timed events",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "tau": tau, "opnorm2_gpu": L},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": 4 * m,
+                    "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "ista_iter_per_s": sep["ista"], "admm_iter_per_s": sep["admm"],
+            "plan_ms": plan_ms, "opnorm_ms_100_iters": opnorm_ms,
+            **extras,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def measure_passes(cs, plan, y, x, z, tau, n, m, flush, stream, torch):
+    """Average launch time of each pass kernel (CUDA events on the plan's
+    stream), back-to-back (L2-warm, as inside a solve) and after an L2 flush
+    (cold).  Returns the roofline record of the dominant kernel."""
+    hbm, src = peaks()
+    per_iter_launches = {0: 1, 1: 1, 2: 1, 3: 1, 4: 1, 5: 1}
+    out = {}
+    for pid in range(6):
+        if pid == 0:
+            cs.cs_ista(plan, y, LAM, tau, 3, x)
+        if pid == 4:
+            cs.cs_admm(plan, y, LAM, RHO, 3, z)
+        reps = 50
+        cs.cs_profile_pass(plan, pid, 5)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        cs.cs_profile_pass(plan, pid, reps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        warm = a.elapsed_time(b) / reps
+        cold = []
+        for _ in range(10):
+            flush.zero_()
+            a.record(stream)
+            cs.cs_profile_pass(plan, pid, 1)
+            b.record(stream)
+            torch.cuda.synchronize()
+            cold.append(a.elapsed_time(b))
+        cold_ms = statistics.median(cold)
+        nbytes = pass_bytes(pid, n, m)
+        out[PASS_NAMES[pid]] = {"warm_us": 1e3 * warm, "cold_us": 1e3 * cold_ms, "alg_bytes": nbytes,
+                                "warm_gbs": nbytes / warm / 1e6, "cold_gbs": nbytes / cold_ms / 1e6}
+    # dominant kernel: largest time per step (each pass runs once per iteration of its solver)
+    dom = max(range(6), key=lambda p: out[PASS_NAMES[p]]["warm_us"] * per_iter_launches[p])
+    d = out[PASS_NAMES[dom]]
+    roof = {"bound": "hbm", "kernel": PASS_NAMES[dom], "achieved": d["warm_gbs"], "peak": hbm,
+            "unit": "GB/s", "frac": d["warm_gbs"] / hbm, "traffic": traffic_record(dom),
+            "peak_source": f"{src} hbm_gbs", "alg_bytes_per_launch": d["alg_bytes"],
+            "cold_l2": {"achieved": d["cold_gbs"], "frac": d["cold_gbs"] / hbm}}
+    return roof, out
+
+
+def time_to_nmse(cs, plan, y, xt, tau, n, dev, torch):
+    """Iterations and stream time to reach NMSE <= 1e-4 (checked every 10
+    iterations, at most 2000), plan time excluded."""
+    res = {}
+    cs.cs_set_monitor(plan, xt, 1e-4, 10)
+    x = torch.zeros(n, dtype=torch.float32, device=dev)
+    st = cs.cs_ista(plan, y, LAM, tau, 2000, x)
+    res["ista"] = {"iters": st["iters_run"], "ms": st["ms"], "nmse": st["nmse"], "reached": bool(st["converged"])}
+    z = torch.zeros(n, dtype=torch.float32, device=dev)
+    st = cs.cs_admm(plan, y, LAM, RHO, 2000, z)
+    res["admm"] = {"iters": st["iters_run"], "ms": st["ms"], "nmse": st["nmse"], "reached": bool(st["converged"])}
+    cs.cs_set_monitor(plan, None, 0.0, 10)
+    return res
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,172 @@
+/*
+ * cs.h -- C ABI of the GB300 circulant compressed-sensing recovery library
+ * (ISTA and ADMM on a partial circulant sensing matrix, arXiv 1707.02244).
+ *
+ * Problem (Sec. 1, Eq. 1 and Eq. 3; Sec. 4.3):
+ *   y = A x* (+ noise),  A = P C,  C the n x n circulant with first row c,
+ *   C[i][j] = c[(j - i) mod n] (Sec. 4.2), P keeping the m distinct rows
+ *   `rows` of C.  Both solvers minimise 0.5 ||y - A x||^2 + lambda ||x||_1,
+ *   which has the minimiser of Eq. 3 with alpha = lambda.
+ *
+ * Conventions shared by every call
+ *   - Vectors passed to a call are DEVICE pointers to fp32 arrays on the
+ *     current device, used on the stream given to cs_plan.  Calls are
+ *     asynchronous with respect to the host unless a cs_stats pointer is
+ *     passed (then the call waits for its own work to finish).
+ *   - y[i] always pairs with row rows[i] as given to cs_plan (any order).
+ *   - The caller owns every vector it passes; the plan owns all of its own
+ *     memory (spectrum, tables, exchange buffer) and frees it in
+ *     cs_plan_destroy.  The plan copies `rows` and `c`.
+ *   - n must be a power of two with 64 <= n <= 4194304 (2^22); 1 <= m <= n.
+ *   - Argument errors are returned at once and nothing is launched.
+ *     Errors found on the device (non-finite input, a wait that ran out) are
+ *     latched in the plan and returned by cs_status_sync or by the next call
+ *     that synchronises.
+ *   - A plan is used from one host thread at a time and one stream.
+ */
+#ifndef CS_H
+#define CS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cs_plan_s* cs_plan_t;
+
+typedef enum {
+  CS_OK = 0,
+  CS_ERR_ARG = 1,          /* bad argument (null, range, duplicate row, ...) */
+  CS_ERR_NOMEM = 2,        /* device allocation failed */
+  CS_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  CS_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out */
+  CS_ERR_NONFINITE = 5,    /* NaN/Inf in y or in the iterates */
+  CS_ERR_UNSUPPORTED = 6   /* size outside the supported set */
+} cs_status;
+
+/* Convergence record of the last check point of a solve.
+ * ISTA: nmse = ||x_T - x*||^2 / ||x*||^2 (NaN without a monitor),
+ *       rel_change = ||x_T - x_{T-1}|| / ||x_T||,
+ *       objective = 0.5 ||y - A x_{T-1}||^2 + lambda ||x_{T-1}||_1.
+ * ADMM: nmse of z_T, rel_change = ||x_T - z_T|| / ||z_T|| (primal residual),
+ *       objective = 0.5 ||y - A x_T||^2 + lambda ||z_T||_1.
+ * ms = elapsed stream time of the call (CUDA events). */
+typedef struct {
+  int iters_run;
+  int converged;      /* 1 when the monitor's NMSE tolerance was met */
+  double nmse;
+  double rel_change;
+  double objective;
+  double ms;
+  int launches;       /* kernels this call enqueued (graph nodes included) */
+} cs_stats;
+
+/* Algorithm 3 parameters, named as in the paper: sigma weighs x = z,
+ * rho weighs v = C x, tau1 / tau2 are the dual steps (converges for
+ * tau1 = tau2 in (0, (sqrt(5)+1)/2), Sec. 4.3). */
+typedef struct {
+  double sigma;
+  double rho;
+  double tau1;
+  double tau2;
+} cs_admm_params;
+
+/* Build a plan for A = P C (Sec. 4.3).
+ *   n, m      signal length and number of measurements
+ *   rows      HOST int64[m], distinct, each in [0, n); any order
+ *   c         HOST float64[n], first row of C (Sec. 4.2)
+ *   stream    cudaStream_t (NULL = legacy default stream)
+ * The spectrum chat = DFT(c) is computed on the GPU in FP64 and rounded to
+ * fp32 tables; for ADMM, B = (rho C^T C + sigma I)^-1 is applied through its
+ * FP64-computed spectrum 1/(rho |chat|^2 + sigma) ("initial inversion" of
+ * Algorithm 3, done by FFT as Sec. 4.3 and Sec. 5.1 describe).
+ * Synchronises the stream.  Errors: CS_ERR_ARG (null pointer, m out of
+ * range, row out of range, duplicate row), CS_ERR_UNSUPPORTED (n),
+ * CS_ERR_NOMEM, CS_ERR_CUDA. */
+cs_status cs_plan(cs_plan_t* out, int64_t n, int64_t m, const int64_t* rows,
+                  const double* c, void* stream);
+
+/* Free the plan and all its device memory (synchronises the stream). */
+cs_status cs_plan_destroy(cs_plan_t plan);
+
+/* ||A||_2^2 by `iters` power iterations on A^T A (products as in
+ * cs_forward / cs_adjoint; fixed seeded start).  A lower estimate that
+ * improves with iters; Algorithm 1 wants tau in (0, ||A||^-2).
+ * Result in *L (HOST double).  Synchronises. */
+cs_status cs_opnorm2(cs_plan_t plan, int iters, double* L);
+
+/* y = A x: x DEVICE float[n] in natural order, y DEVICE float[m] with
+ * y[i] = (C x)[rows[i]] (Algorithm 1, residual step; Sec. 4.3). */
+cs_status cs_forward(cs_plan_t plan, const float* x, float* y);
+
+/* x = A^T r = C^T P^T r: r DEVICE float[m] paired with rows, x DEVICE
+ * float[n] (Algorithm 1, gradient step). */
+cs_status cs_adjoint(cs_plan_t plan, const float* r, float* x);
+
+/* Attach a ground truth for NMSE monitoring.
+ *   x_true     DEVICE float[n] (caller keeps it alive while the plan uses
+ *              it) or NULL to detach
+ *   nmse_tol   stop a solve once NMSE <= nmse_tol at a check point (<= 0:
+ *              never stop early; NMSE is still reported)
+ *   check_every  iterations between check points (>= 1; default 10)
+ * Sec. 6 counts a signal as recovered once its error reaches 1e-4.
+ * Synchronises (computes ||x*||^2 on the device). */
+cs_status cs_set_monitor(cs_plan_t plan, const float* x_true, double nmse_tol,
+                         int check_every);
+
+/* ISTA (Algorithm 1) for `iters` iterations (fewer if the monitor stops it):
+ *   r = y - A x;  x <- eta_{tau*lambda}(x + tau A^T r)   (Eq. 4 threshold)
+ *   y      DEVICE float[m] paired with rows
+ *   x      DEVICE float[n], in: x(0) (the paper starts from 0), out: x(T)
+ *   stats  HOST cs_stats* or NULL (non-NULL: the call synchronises)
+ * Errors: CS_ERR_ARG (null, lambda < 0, tau <= 0, iters < 0). */
+cs_status cs_ista(cs_plan_t plan, const float* y, float lambda, float tau,
+                  int iters, float* x, cs_stats* stats);
+
+/* ADMM (Algorithm 3) from the zero state with sigma = rho = `rho` and
+ * tau1 = tau2 = 1; z DEVICE float[n] receives the sparse estimate z(T).
+ * Errors: CS_ERR_ARG (null, lambda < 0, rho <= 0, iters < 0). */
+cs_status cs_admm(cs_plan_t plan, const float* y, float lambda, float rho,
+                  int iters, float* z, cs_stats* stats);
+
+/* ADMM (Algorithm 3) with every parameter and the state exposed.
+ *   v, z, mu, nu  DEVICE float[n] each, the state of Algorithm 3 (v is the
+ *                 folded v + mu of the loop's last line).  warm = 0: the
+ *                 state is set to zero first (the paper's start); warm = 1:
+ *                 the given state is the starting point.  On return they
+ *                 hold the state after the last iteration.
+ *   x             DEVICE float[n] or NULL: receives x(T)
+ * Errors: CS_ERR_ARG (null state, sigma/rho <= 0, tau1/tau2 <= 0). */
+cs_status cs_admm_ex(cs_plan_t plan, const float* y, float lambda,
+                     const cs_admm_params* params, int iters, int warm,
+                     float* x, float* z, float* mu, float* nu, float* v,
+                     cs_stats* stats);
+
+/* Measurement hook (no counterpart in the paper; Sec. 6 reports throughput
+ * in iterations per second).  Enqueue `reps` back-to-back launches of one
+ * pass kernel of the iteration on the plan's stream, reusing the arguments
+ * of the plan's last cs_ista / cs_admm_ex call (the buffers it named must
+ * still be alive; the pass overwrites them as a real iteration would):
+ *   0 mid pass C x      1 column pass residual   2 mid pass C^T r
+ *   3 column pass ISTA update                   4 mid pass ADMM x-update
+ *   5 column pass ADMM updates
+ * For timing with CUDA events around the call.  Errors: CS_ERR_ARG
+ * (pass_id, reps < 1, no earlier solve of that kind). */
+cs_status cs_profile_pass(cs_plan_t plan, int pass_id, int reps);
+
+/* Wait for the plan's stream and return the latched device status
+ * (CS_OK, CS_ERR_NONFINITE, CS_ERR_TIMEOUT), then clear it. */
+cs_status cs_status_sync(cs_plan_t plan);
+
+/* Static, human-readable name of a status code. */
+const char* cs_status_string(cs_status s);
+
+/* Library ABI version (major * 100 + minor). */
+int cs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CS_H */

@@ -35,7 +35,8 @@ import numpy as np
 __all__ = [
     "circulant_matrix", "sensing_matrix", "soft_threshold", "lasso_objective",
     "kkt_violation", "forward_dense", "adjoint_dense", "spectrum",
-    "forward_fft", "adjoint_fft", "circulant_apply_fft", "ista_dense",
+    "forward_fft", "adjoint_fft", "circulant_apply_fft", "forward_sampled",
+    "adjoint_sampled", "zero_fill", "ista_dense",
     "ista_fft", "admm_dense", "admm_fft", "admm_standard_dense",
     "admm_d_diagonal", "opnorm2_dense", "opnorm2_power_fft",
     "lasso_bruteforce", "l0_bruteforce", "nmse", "naive_dft",
@@ -92,16 +93,40 @@ def circulant_apply_fft(chat: np.ndarray, x: np.ndarray, transpose: bool = False
     """C x (or C^T x) through the convolution theorem.
 
     With ``C[i, j] = c[(j - i) mod n]`` and real c, ``FFT(C x) = conj(chat) *
-    FFT(x)`` and ``FFT(C^T x) = chat * FFT(x)``.
+    FFT(x)`` and ``FFT(C^T x) = chat * FFT(x)``.  x and the result are real,
+    so only bins 0..n/2 are formed (real-input FFT).
     """
-    xh = np.fft.fft(np.asarray(x, dtype=np.float64))
-    h = chat if transpose else np.conj(chat)
-    return np.fft.ifft(h * xh).real
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    xh = np.fft.rfft(x)                   # bins 0..n/2 of the real input
+    h = chat[: n // 2 + 1]
+    h = h if transpose else np.conj(h)
+    return np.fft.irfft(h * xh, n)
 
 
 def forward_fft(chat, rows, x):
     """A x = (C x)[rows] (Sec. 4.3) with C x taken by FFT."""
     return circulant_apply_fft(chat, x)[np.asarray(rows, dtype=np.int64)]
+
+
+def forward_sampled(c, rows, x, idx):
+    """Entries ``idx`` of A x, each by its own O(n) dot product with the
+    shifted generating vector: ``(A x)_i = sum_j c[(j - rows[i]) mod n] x_j``
+    (Sec. 4.2 index rule).  For full-size checks where A cannot be formed."""
+    c = np.asarray(c, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    rows = np.asarray(rows, dtype=np.int64)
+    return np.array([float(np.roll(c, int(rows[i])) @ x) for i in idx])
+
+
+def adjoint_sampled(c, rows, r, idx):
+    """Entries ``idx`` of A^T r, each by its own O(m) sum:
+    ``(A^T r)_j = sum_i c[(j - rows[i]) mod n] r_i``."""
+    c = np.asarray(c, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    rows = np.asarray(rows, dtype=np.int64)
+    n = c.shape[0]
+    return np.array([float(c[(int(j) - rows) % n] @ r) for j in idx])
 
 
 def zero_fill(n: int, rows, r):
@@ -263,7 +288,7 @@ def admm_fft(c, rows, y, lam, sigma, rho, tau1=1.0, tau2=1.0, iters=100,
     bhat = 1.0 / (rho * np.abs(chat) ** 2 + sigma)
 
     def B_apply(b):
-        return np.fft.ifft(bhat * np.fft.fft(b)).real
+        return np.fft.irfft(bhat[: n // 2 + 1] * np.fft.rfft(b), n)
 
     return _admm(lambda v: circulant_apply_fft(chat, v),
                  lambda v: circulant_apply_fft(chat, v, transpose=True),

@@ -1,0 +1,216 @@
+"""Python binding of libcsgb (circulant LASSO recovery on GB300).
+
+Argument marshalling only: every step of ISTA / ADMM runs in the CUDA
+library.  The names are those of the C ABI in ``include/cs.h``.  Device
+vectors may be given as torch CUDA tensors (float32, contiguous) or as raw
+device addresses (int); host arrays (rows, c) as numpy arrays.
+
+The library is required: importing this package on a machine where
+``libcsgb.so`` has not been built raises ``ImportError`` (there is no CPU
+fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import pathlib
+
+import numpy as np
+
+_PKG = pathlib.Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libcsgb.so"
+
+CS_OK, CS_ERR_ARG, CS_ERR_NOMEM, CS_ERR_CUDA, CS_ERR_TIMEOUT, CS_ERR_NONFINITE, CS_ERR_UNSUPPORTED = range(7)
+
+EXPORTS = ("cs_plan", "cs_plan_destroy", "cs_opnorm2", "cs_forward", "cs_adjoint",
+           "cs_set_monitor", "cs_ista", "cs_admm", "cs_admm_ex", "cs_status_sync",
+           "cs_status_string", "cs_version", "cs_profile_pass")
+
+
+class CsStats(ctypes.Structure):
+    _fields_ = [("iters_run", ctypes.c_int), ("converged", ctypes.c_int),
+                ("nmse", ctypes.c_double), ("rel_change", ctypes.c_double),
+                ("objective", ctypes.c_double), ("ms", ctypes.c_double),
+                ("launches", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class CsAdmmParams(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("rho", ctypes.c_double),
+                ("tau1", ctypes.c_double), ("tau2", ctypes.c_double)]
+
+
+class CsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+
+
+def _load() -> ctypes.CDLL:
+    if not LIB_PATH.exists():
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(str(LIB_PATH))
+    vp, i64, f32, f64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_float, ctypes.c_double, ctypes.c_int
+    sig = {
+        "cs_plan": [ctypes.POINTER(vp), i64, i64, vp, vp, vp],
+        "cs_plan_destroy": [vp],
+        "cs_opnorm2": [vp, ci, ctypes.POINTER(f64)],
+        "cs_forward": [vp, vp, vp],
+        "cs_adjoint": [vp, vp, vp],
+        "cs_set_monitor": [vp, vp, f64, ci],
+        "cs_ista": [vp, vp, f32, f32, ci, vp, ctypes.POINTER(CsStats)],
+        "cs_admm": [vp, vp, f32, f32, ci, vp, ctypes.POINTER(CsStats)],
+        "cs_admm_ex": [vp, vp, f32, ctypes.POINTER(CsAdmmParams), ci, ci, vp, vp, vp, vp, vp,
+                       ctypes.POINTER(CsStats)],
+        "cs_status_sync": [vp],
+        "cs_profile_pass": [vp, ci, ci],
+        "cs_status_string": [ci],
+        "cs_version": [],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.cs_status_string.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def status_string(code: int) -> str:
+    return _lib.cs_status_string(int(code)).decode()
+
+
+def cs_version() -> int:
+    return int(_lib.cs_version())
+
+
+def _ptr(t) -> int | None:
+    """Device address of a tensor-like (torch tensor, int, None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        if getattr(t, "dtype", None) is not None and str(t.dtype) != "torch.float32":
+            raise TypeError(f"expected float32, got {t.dtype}")
+        if hasattr(t, "is_contiguous") and not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        if hasattr(t, "is_cuda") and not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        return int(t.data_ptr())
+    raise TypeError(f"cannot take a device pointer of {type(t)!r}")
+
+
+def _check(code: int, where: str):
+    if code != CS_OK:
+        raise CsError(code, where)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """Owns a cs_plan_t; closes it on ``close()`` or garbage collection."""
+
+    def __init__(self, handle: int, n: int, m: int):
+        self.handle = handle
+        self.n = n
+        self.m = m
+
+    def close(self):
+        if self.handle:
+            _lib.cs_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cs_plan(n: int, m: int, rows, c, stream=None) -> Plan:
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    if rows.shape != (m,) or c.shape != (n,):
+        raise ValueError("rows must have shape (m,) and c shape (n,)")
+    h = ctypes.c_void_p()
+    code = _lib.cs_plan(ctypes.byref(h), n, m, rows.ctypes.data, c.ctypes.data, _stream_handle(stream))
+    _check(code, "cs_plan")
+    return Plan(h.value, n, m)
+
+
+def cs_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def cs_opnorm2(plan: Plan, iters: int = 100) -> float:
+    L = ctypes.c_double()
+    _check(_lib.cs_opnorm2(plan.handle, iters, ctypes.byref(L)), "cs_opnorm2")
+    return L.value
+
+
+def cs_forward(plan: Plan, x, y):
+    _check(_lib.cs_forward(plan.handle, _ptr(x), _ptr(y)), "cs_forward")
+
+
+def cs_adjoint(plan: Plan, r, x):
+    _check(_lib.cs_adjoint(plan.handle, _ptr(r), _ptr(x)), "cs_adjoint")
+
+
+def cs_set_monitor(plan: Plan, x_true=None, nmse_tol: float = 0.0, check_every: int = 10):
+    _check(_lib.cs_set_monitor(plan.handle, _ptr(x_true), float(nmse_tol), int(check_every)),
+           "cs_set_monitor")
+
+
+def cs_ista(plan: Plan, y, lam: float, tau: float, iters: int, x, stats: bool = True):
+    st = CsStats()
+    code = _lib.cs_ista(plan.handle, _ptr(y), lam, tau, iters, _ptr(x), ctypes.byref(st) if stats else None)
+    _check(code, "cs_ista")
+    return st.as_dict() if stats else None
+
+
+def cs_admm(plan: Plan, y, lam: float, rho: float, iters: int, z, stats: bool = True):
+    st = CsStats()
+    code = _lib.cs_admm(plan.handle, _ptr(y), lam, rho, iters, _ptr(z), ctypes.byref(st) if stats else None)
+    _check(code, "cs_admm")
+    return st.as_dict() if stats else None
+
+
+def cs_admm_ex(plan: Plan, y, lam: float, sigma: float, rho: float, tau1: float, tau2: float,
+               iters: int, warm: bool, x, z, mu, nu, v, stats: bool = True):
+    st = CsStats()
+    prm = CsAdmmParams(sigma, rho, tau1, tau2)
+    code = _lib.cs_admm_ex(plan.handle, _ptr(y), lam, ctypes.byref(prm), iters, int(bool(warm)),
+                           _ptr(x), _ptr(z), _ptr(mu), _ptr(nu), _ptr(v),
+                           ctypes.byref(st) if stats else None)
+    _check(code, "cs_admm_ex")
+    return st.as_dict() if stats else None
+
+
+def cs_profile_pass(plan: Plan, pass_id: int, reps: int = 1):
+    _check(_lib.cs_profile_pass(plan.handle, int(pass_id), int(reps)), "cs_profile_pass")
+
+
+def cs_status_sync(plan: Plan) -> int:
+    return int(_lib.cs_status_sync(plan.handle))
+
+
+def raw_call(name: str, *args) -> int:
+    """Call a C entry point with raw ctypes arguments and return its status
+    (used by the C-ABI contract tests)."""
+    return int(getattr(_lib, name)(*args))
+
+
+def nan_to_none(v: float):
+    return None if (v is None or (isinstance(v, float) and math.isnan(v))) else v

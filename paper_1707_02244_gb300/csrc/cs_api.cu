@@ -1,0 +1,621 @@
+// Host runtime of the C ABI declared in include/cs.h: plan construction,
+// argument checks, CUDA-graph capture of the iteration loop, monitoring.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+
+#include "../../include/cs.h"
+#include "cs_fft.cuh"
+#include "cs_internal.h"
+
+using namespace csk;
+
+struct cs_plan_s {
+  int64_t n = 0, m = 0;
+  cudaStream_t stream = nullptr;   // caller's stream
+  cudaStream_t cap = nullptr;      // private stream used only for graph capture
+  Geo gi{}, ga{};                  // real-FFT (N = n/2) and complex-n (N = n) geometry
+  float2* W = nullptr;
+  uint32_t* mask = nullptr;
+  uint32_t* prefix = nullptr;
+  int32_t* pos = nullptr;
+  int32_t* rows32 = nullptr;
+  float* ys = nullptr;
+  double* partials = nullptr;
+  double* stats = nullptr;
+  int* status = nullptr;
+  CallArgs* ca = nullptr;
+  float4* tab_ista = nullptr;
+  float2* tab_admm_c = nullptr;
+  float* tab_admm_b = nullptr;
+  double* abs2 = nullptr;
+  float2* twi = nullptr;
+  float2* twa = nullptr;
+  float* dense = nullptr;
+  float* dense2 = nullptr;
+  float* dense3 = nullptr;
+  double* host_stats = nullptr;    // pinned [NSTAT]
+  int* host_status = nullptr;      // pinned
+  double b_rho = -1.0, b_sigma = -1.0;
+  const float* xtrue = nullptr;
+  double xtrue2 = 0.0;
+  double tol = 0.0;
+  int check_every = 10;
+  bool use_graphs = true;
+  int latched = 0;                 // device status bits read back but not yet reported
+  int launches = 0;                // kernels enqueued by the current call
+  int graph_nodes_last = 0;
+  bool ista_args = false, admm_args = false;   // last solve of each kind left valid arguments
+  std::map<uint64_t, int> graph_nodes;
+  std::map<uint64_t, cudaGraphExec_t> graphs;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) ++l;
+  return l;
+}
+
+void make_geo(Geo& g, int lgN) {
+  constexpr int lgTILE = 13;   // TILE = 8192
+  g.lgN = lgN;
+  g.N = 1 << lgN;
+  g.lgN2 = lgN / 2 < 10 ? lgN / 2 : 10;
+  g.N2 = 1 << g.lgN2;
+  g.lgN1 = lgN - g.lgN2;
+  g.N1 = 1 << g.lgN1;
+  g.lgG = (lgTILE - g.lgN2) < g.lgN1 ? (lgTILE - g.lgN2) : g.lgN1;
+  g.G = 1 << g.lgG;
+  g.col_ctas = g.N1 >> g.lgG;
+  const int lgUmax = lgTILE - 1 - g.lgN1;
+  const int lgUnits = g.lgN2 - 1;
+  g.lgU = lgUmax < lgUnits ? lgUmax : lgUnits;
+  g.U = 1 << g.lgU;
+  g.mid_ctas = (g.N2 >> 1) >> g.lgU;
+}
+
+int64_t tab_count(const Geo& g) { return ((int64_t)(g.N2 >> 1) << g.lgN1) + 1; }
+
+cs_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return CS_OK;
+  if (e == cudaErrorMemoryAllocation) return CS_ERR_NOMEM;
+  return CS_ERR_CUDA;
+}
+
+#define CS_TRY(expr)                                   \
+  do {                                                 \
+    cudaError_t e_ = (expr);                           \
+    if (e_ != cudaSuccess) return cuda_status(e_);     \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 256);
+}
+
+void free_plan(cs_plan_s* p) {
+  if (!p) return;
+  for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
+  void* bufs[] = {p->W, p->mask, p->prefix, p->pos, p->rows32, p->ys, p->partials, p->stats, p->status,
+                  p->ca, p->tab_ista, p->tab_admm_c, p->tab_admm_b, p->abs2, p->twi, p->twa,
+                  p->dense, p->dense2, p->dense3};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (p->host_stats) cudaFreeHost(p->host_stats);
+  if (p->host_status) cudaFreeHost(p->host_status);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  delete p;
+}
+
+KParams kparams(const cs_plan_s* p, const Geo& g, int flags) {
+  KParams k;
+  k.geo = g;
+  k.pp.W = p->W;
+  k.pp.mask = p->mask;
+  k.pp.prefix = p->prefix;
+  k.pp.ys = p->ys;
+  k.pp.partials = p->partials;
+  k.pp.stats = p->stats;
+  k.pp.tab_ista = p->tab_ista;
+  k.pp.tab_admm_c = p->tab_admm_c;
+  k.pp.tab_admm_b = p->tab_admm_b;
+  k.pp.status = p->status;
+  k.ca = p->ca;
+  k.flags = flags;
+  return k;
+}
+
+cudaError_t make_tables(Geo& g, float2* base, cudaStream_t s) {
+  // tw1 [2 N1] | tw2 [N2] | twl [N1] | twr [N2]
+  float2* tw1 = base;
+  float2* tw2 = tw1 + 2 * g.N1;
+  float2* twl = tw2 + g.N2;
+  float2* twr = twl + g.N1;
+  cudaError_t e = launch_twiddle(tw1, 2 * g.N1, 2 * (int64_t)g.N1, s);
+  if (e == cudaSuccess) e = launch_twiddle(tw2, g.N2, g.N2, s);
+  if (e == cudaSuccess) e = launch_twiddle(twl, g.N1, g.N, s);
+  if (e == cudaSuccess) e = launch_twiddle(twr, g.N2, 2 * (int64_t)g.N, s);
+  g.tw1 = tw1;
+  g.tw2 = tw2;
+  g.twl = twl;
+  g.twr = twr;
+  return e;
+}
+
+size_t twiddle_count(const Geo& g) { return 3 * (size_t)g.N1 + 2 * (size_t)g.N2; }
+
+// Read the device status word and the finalised stats into pinned memory.
+cudaError_t read_back(cs_plan_s* p) {
+  cudaError_t e = cudaMemcpyAsync(p->host_stats, p->stats, NSTAT * sizeof(double), cudaMemcpyDeviceToHost,
+                                  p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->host_status, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e == cudaSuccess) p->latched |= *p->host_status;
+  return e;
+}
+
+cs_status latched_status(cs_plan_s* p) {
+  if (p->latched & STS_TIMEOUT) return CS_ERR_TIMEOUT;
+  if (p->latched & STS_NONFINITE) return CS_ERR_NONFINITE;
+  return CS_OK;
+}
+
+// One solve chunk: `len` iterations, the last of which computes the check
+// statistics; `final_chunk` drops the forward FFT after the last update.
+enum SolveKind { K_ISTA = 1, K_ADMM = 2 };
+
+cudaError_t enqueue_chunk(cs_plan_s* p, SolveKind kind, int len, bool final_chunk, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (int it = 0; it < len && e == cudaSuccess; ++it) {
+    const bool last = it == len - 1;
+    const int flags = last ? (FL_STATS | FL_WRITE_STATE) : 0;
+    if (kind == K_ISTA) {
+      const Geo& g = p->gi;
+      e = launch_mid(MID_FWD, kparams(p, g, 0), s);
+      if (e == cudaSuccess) e = launch_col(COL_RESIDUAL, kparams(p, g, flags), s);
+      if (e == cudaSuccess) e = launch_mid(MID_ADJ, kparams(p, g, 0), s);
+      if (e == cudaSuccess)
+        e = launch_col((last && final_chunk) ? COL_ISTA_LAST : COL_ISTA, kparams(p, g, flags), s);
+      if (e == cudaSuccess && last) e = launch_finalize(p->partials, g.col_ctas, p->stats, s);
+    } else {
+      const Geo& g = p->ga;
+      e = launch_mid(MID_ADMM, kparams(p, g, 0), s);
+      if (e == cudaSuccess)
+        e = launch_col((last && final_chunk) ? COL_ADMM_LAST : COL_ADMM, kparams(p, g, flags), s);
+      if (e == cudaSuccess && last) e = launch_finalize(p->partials, g.col_ctas, p->stats, s);
+    }
+  }
+  return e;
+}
+
+int chunk_kernels(SolveKind kind, int len) { return (kind == K_ISTA ? 4 : 2) * len + 1; }
+
+cudaError_t run_chunk(cs_plan_s* p, SolveKind kind, int len, bool final_chunk) {
+  p->launches += chunk_kernels(kind, len);
+  if (!p->use_graphs) return enqueue_chunk(p, kind, len, final_chunk, p->stream);
+  const uint64_t key = ((uint64_t)kind << 40) | ((uint64_t)final_chunk << 32) | (uint32_t)len;
+  auto it = p->graphs.find(key);
+  if (it == p->graphs.end()) {
+    cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t e2 = enqueue_chunk(p, kind, len, final_chunk, p->cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(p->cap, &graph);
+    if (e2 != cudaSuccess || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return e2 != cudaSuccess ? e2 : e;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    it = p->graphs.emplace(key, exec).first;
+  }
+  return cudaGraphLaunch(it->second, p->stream);
+}
+
+// Iterate in chunks of check_every; with a monitor tolerance, stop at the
+// first check point whose NMSE meets it.
+cudaError_t solve_loop(cs_plan_s* p, SolveKind kind, int iters, int* iters_run, int* converged,
+                       bool need_stats) {
+  *iters_run = 0;
+  *converged = 0;
+  const int ce = p->check_every;
+  const bool watch = p->xtrue != nullptr && p->tol > 0.0;
+  int done = 0;
+  while (done < iters) {
+    const int len = (iters - done) < ce ? (iters - done) : ce;
+    const bool final_chunk = done + len == iters;
+    cudaError_t e = run_chunk(p, kind, len, final_chunk);
+    if (e != cudaSuccess) return e;
+    done += len;
+    if (watch && !final_chunk) {
+      e = read_back(p);
+      if (e != cudaSuccess) return e;
+      const double nm = p->host_stats[ST_ERR2] / p->xtrue2;
+      if (p->host_stats[ST_NONFIN] > 0.0) p->latched |= STS_NONFINITE;
+      if (nm <= p->tol || (p->latched & STS_NONFINITE)) {
+        *converged = nm <= p->tol;
+        break;
+      }
+    }
+  }
+  *iters_run = done;
+  if ((need_stats || watch) && done > 0) {
+    cudaError_t e = read_back(p);
+    if (e != cudaSuccess) return e;
+    if (p->host_stats[ST_NONFIN] > 0.0) p->latched |= STS_NONFINITE;
+    if (watch) *converged = p->host_stats[ST_ERR2] / p->xtrue2 <= p->tol;
+  }
+  return cudaSuccess;
+}
+
+void fill_stats(const cs_plan_s* p, cs_stats* st, int iters_run, int converged, double lambda, bool admm) {
+  const double* h = p->host_stats;
+  st->iters_run = iters_run;
+  st->converged = converged;
+  st->launches = p->launches;
+  if (iters_run == 0) {
+    st->nmse = NAN;
+    st->rel_change = NAN;
+    st->objective = NAN;
+    return;
+  }
+  st->nmse = p->xtrue ? h[ST_ERR2] / p->xtrue2 : NAN;
+  st->rel_change = h[ST_X2] > 0.0 ? std::sqrt(h[ST_DX2] / h[ST_X2]) : (h[ST_DX2] > 0.0 ? INFINITY : 0.0);
+  st->objective = 0.5 * h[ST_R2] + lambda * h[ST_L1];
+  st->launches = p->launches;
+  (void)admm;
+}
+
+bool valid_ptr(const void* q) { return q != nullptr && ((uintptr_t)q & 7u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int cs_version(void) { return 100; }
+
+const char* cs_status_string(cs_status s) {
+  switch (s) {
+    case CS_OK: return "CS_OK";
+    case CS_ERR_ARG: return "CS_ERR_ARG";
+    case CS_ERR_NOMEM: return "CS_ERR_NOMEM";
+    case CS_ERR_CUDA: return "CS_ERR_CUDA";
+    case CS_ERR_TIMEOUT: return "CS_ERR_TIMEOUT";
+    case CS_ERR_NONFINITE: return "CS_ERR_NONFINITE";
+    case CS_ERR_UNSUPPORTED: return "CS_ERR_UNSUPPORTED";
+  }
+  return "CS_UNKNOWN";
+}
+
+cs_status cs_plan(cs_plan_t* out, int64_t n, int64_t m, const int64_t* rows, const double* c, void* stream) {
+  if (!out || !rows || !c) return CS_ERR_ARG;
+  *out = nullptr;
+  if (m < 1 || m > n) return CS_ERR_ARG;
+  if (n < 64 || n > (int64_t(1) << 22) || (n & (n - 1)) != 0) return CS_ERR_UNSUPPORTED;
+  cs_plan_s* p = new (std::nothrow) cs_plan_s();
+  if (!p) return CS_ERR_NOMEM;
+  p->n = n;
+  p->m = m;
+  p->stream = static_cast<cudaStream_t>(stream);
+  const char* env = std::getenv("CS_GRAPHS");
+  p->use_graphs = !(env && env[0] == '0');
+  const int lgn = ilog2(n);
+  make_geo(p->gi, lgn - 1);
+  make_geo(p->ga, lgn);
+
+  int64_t* d_rows = nullptr;
+  double* d_c = nullptr;
+  double2* fa = nullptr;
+  double2* fb = nullptr;
+  cs_status st = CS_OK;
+  auto fail = [&](cs_status s) {
+    if (d_rows) cudaFree(d_rows);
+    if (d_c) cudaFree(d_c);
+    if (fa) cudaFree(fa);
+    if (fb) cudaFree(fb);
+    free_plan(p);
+    return s;
+  };
+#define CS_PLAN_TRY(expr)                                  \
+  do {                                                     \
+    cudaError_t e_ = (expr);                               \
+    if (e_ != cudaSuccess) return fail(cuda_status(e_));   \
+  } while (0)
+
+  CS_PLAN_TRY(init_pass_kernels());
+  CS_PLAN_TRY(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+  CS_PLAN_TRY(cudaEventCreate(&p->ev0));
+  CS_PLAN_TRY(cudaEventCreate(&p->ev1));
+  const int64_t words = n / 32;
+  const int maxctas = p->ga.col_ctas > p->gi.col_ctas ? p->ga.col_ctas : p->gi.col_ctas;
+  const int64_t npart = (int64_t)maxctas * NSTAT > 256 ? (int64_t)maxctas * NSTAT : 256;
+  CS_PLAN_TRY(dalloc(&p->W, n));
+  CS_PLAN_TRY(dalloc(&p->mask, words));
+  CS_PLAN_TRY(dalloc(&p->prefix, words));
+  CS_PLAN_TRY(dalloc(&p->pos, m));
+  CS_PLAN_TRY(dalloc(&p->rows32, m));
+  CS_PLAN_TRY(dalloc(&p->ys, m));
+  CS_PLAN_TRY(dalloc(&p->partials, npart));
+  CS_PLAN_TRY(dalloc(&p->stats, NSTAT));
+  CS_PLAN_TRY(dalloc(&p->status, 1));
+  CS_PLAN_TRY(dalloc(&p->ca, 1));
+  CS_PLAN_TRY(dalloc(&p->tab_ista, tab_count(p->gi)));
+  CS_PLAN_TRY(dalloc(&p->tab_admm_c, tab_count(p->ga)));
+  CS_PLAN_TRY(dalloc(&p->tab_admm_b, tab_count(p->ga)));
+  CS_PLAN_TRY(dalloc(&p->abs2, tab_count(p->ga)));
+  CS_PLAN_TRY(dalloc(&p->twi, twiddle_count(p->gi)));
+  CS_PLAN_TRY(dalloc(&p->twa, twiddle_count(p->ga)));
+  CS_PLAN_TRY(dalloc(&p->dense, n));
+  CS_PLAN_TRY(dalloc(&p->dense2, n));
+  CS_PLAN_TRY(dalloc(&p->dense3, n));
+  CS_PLAN_TRY(cudaMallocHost(reinterpret_cast<void**>(&p->host_stats), NSTAT * sizeof(double)));
+  CS_PLAN_TRY(cudaMallocHost(reinterpret_cast<void**>(&p->host_status), sizeof(int)));
+  CS_PLAN_TRY(dalloc(&d_rows, m));
+  CS_PLAN_TRY(dalloc(&d_c, n));
+  CS_PLAN_TRY(dalloc(&fa, n));
+  CS_PLAN_TRY(dalloc(&fb, n));
+
+  cudaStream_t s = p->stream;
+  CS_PLAN_TRY(cudaMemcpyAsync(d_rows, rows, m * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CS_PLAN_TRY(cudaMemcpyAsync(d_c, c, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  CS_PLAN_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), s));
+  CS_PLAN_TRY(cudaMemsetAsync(p->mask, 0, words * sizeof(uint32_t), s));
+  CS_PLAN_TRY(cudaMemsetAsync(p->stats, 0, NSTAT * sizeof(double), s));
+  CS_PLAN_TRY(make_tables(p->gi, p->twi, s));
+  CS_PLAN_TRY(make_tables(p->ga, p->twa, s));
+  double2* chat = nullptr;
+  CS_PLAN_TRY(launch_fft64(d_c, fa, fb, n, &chat, s));
+  CS_PLAN_TRY(launch_tab_ista(chat, p->gi, n, p->tab_ista, s));
+  CS_PLAN_TRY(launch_tab_admm(chat, p->ga, n, p->tab_admm_c, p->abs2, s));
+  CS_PLAN_TRY(launch_tab_admm_b(p->abs2, (int)tab_count(p->ga), n, 1.0, 1.0, p->tab_admm_b, s));
+  p->b_rho = 1.0;
+  p->b_sigma = 1.0;
+  CS_PLAN_TRY(launch_build_mask(d_rows, m, n, p->mask, p->status, s));
+  CS_PLAN_TRY(launch_prefix(p->mask, words, p->prefix, s));
+  CS_PLAN_TRY(cudaMemcpyAsync(p->host_status, p->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CS_PLAN_TRY(cudaStreamSynchronize(s));
+  if (*p->host_status & (STS_BAD_ROW | STS_DUP_ROW)) return fail(CS_ERR_ARG);
+  CS_PLAN_TRY(launch_row_pos(d_rows, m, p->mask, p->prefix, p->pos, p->rows32, s));
+  CS_PLAN_TRY(cudaStreamSynchronize(s));
+#undef CS_PLAN_TRY
+  cudaFree(d_rows);
+  cudaFree(d_c);
+  cudaFree(fa);
+  cudaFree(fb);
+  (void)st;
+  *out = p;
+  return CS_OK;
+}
+
+cs_status cs_plan_destroy(cs_plan_t plan) {
+  if (!plan) return CS_ERR_ARG;
+  cudaStreamSynchronize(plan->stream);
+  free_plan(plan);
+  return CS_OK;
+}
+
+cs_status cs_status_sync(cs_plan_t p) {
+  if (!p) return CS_ERR_ARG;
+  CS_TRY(cudaMemcpyAsync(p->host_status, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CS_TRY(cudaStreamSynchronize(p->stream));
+  p->latched |= *p->host_status;
+  const cs_status s = latched_status(p);
+  p->latched = 0;
+  CS_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
+  return s;
+}
+
+cs_status cs_forward(cs_plan_t p, const float* x, float* y) {
+  if (!p || !valid_ptr(x) || !y) return CS_ERR_ARG;
+  CallArgs a{};
+  a.src = x;
+  a.dst = p->dense;
+  cudaStream_t s = p->stream;
+  p->ista_args = p->admm_args = false;
+  CS_TRY(launch_set_args(a, p->ca, s));
+  CS_TRY(launch_col(COL_LOAD, kparams(p, p->gi, 0), s));
+  CS_TRY(launch_mid(MID_FWD, kparams(p, p->gi, 0), s));
+  CS_TRY(launch_col(COL_STORE, kparams(p, p->gi, 0), s));
+  CS_TRY(launch_gather_rows(p->dense, p->rows32, p->m, y, s));
+  return CS_OK;
+}
+
+cs_status cs_adjoint(cs_plan_t p, const float* r, float* x) {
+  if (!p || !r || !valid_ptr(x)) return CS_ERR_ARG;
+  cudaStream_t s = p->stream;
+  CS_TRY(cudaMemsetAsync(p->dense, 0, p->n * sizeof(float), s));
+  CS_TRY(launch_scatter_rows(r, p->rows32, p->m, p->dense, s));
+  CallArgs a{};
+  a.src = p->dense;
+  a.dst = x;
+  p->ista_args = p->admm_args = false;
+  CS_TRY(launch_set_args(a, p->ca, s));
+  CS_TRY(launch_col(COL_LOAD, kparams(p, p->gi, 0), s));
+  CS_TRY(launch_mid(MID_ADJ, kparams(p, p->gi, 0), s));
+  CS_TRY(launch_col(COL_STORE, kparams(p, p->gi, 0), s));
+  return CS_OK;
+}
+
+cs_status cs_opnorm2(cs_plan_t p, int iters, double* L) {
+  if (!p || !L || iters < 1) return CS_ERR_ARG;
+  cudaStream_t s = p->stream;
+  CS_TRY(launch_power_init(p->dense2, p->n, s));
+  CS_TRY(launch_norm2(p->dense2, p->n, p->partials, p->stats + ST_X2, s));
+  CallArgs a{};
+  a.src = p->dense2;
+  a.aux = p->dense;
+  a.dst = p->dense2;
+  p->ista_args = p->admm_args = false;
+  CS_TRY(launch_set_args(a, p->ca, s));
+  for (int it = 0; it < iters; ++it) {
+    CS_TRY(launch_col(COL_LOAD_SCALED, kparams(p, p->gi, 0), s));
+    CS_TRY(launch_mid(MID_FWD, kparams(p, p->gi, 0), s));
+    CS_TRY(launch_col(COL_MASK, kparams(p, p->gi, 0), s));
+    CS_TRY(launch_mid(MID_ADJ, kparams(p, p->gi, 0), s));
+    CS_TRY(launch_col(COL_POWER_OUT, kparams(p, p->gi, FL_STATS), s));
+    CS_TRY(launch_finalize(p->partials, p->gi.col_ctas, p->stats, s));
+  }
+  CS_TRY(read_back(p));
+  *L = p->host_stats[ST_DX2];
+  return latched_status(p);
+}
+
+cs_status cs_set_monitor(cs_plan_t p, const float* x_true, double nmse_tol, int check_every) {
+  if (!p || check_every < 1) return CS_ERR_ARG;
+  if (x_true && !valid_ptr(x_true)) return CS_ERR_ARG;
+  p->check_every = check_every;
+  p->tol = nmse_tol;
+  p->xtrue = x_true;
+  p->xtrue2 = 0.0;
+  if (x_true) {
+    CS_TRY(launch_norm2(x_true, p->n, p->partials, p->stats + ST_ERR2, p->stream));
+    CS_TRY(read_back(p));
+    p->xtrue2 = p->host_stats[ST_ERR2];
+    if (!(p->xtrue2 > 0.0)) {
+      p->xtrue = nullptr;
+      return CS_ERR_ARG;
+    }
+  }
+  return CS_OK;
+}
+
+cs_status cs_ista(cs_plan_t p, const float* y, float lambda, float tau, int iters, float* x, cs_stats* stats) {
+  if (!p || !y || !valid_ptr(x) || !(lambda >= 0.f) || !(tau > 0.f) || iters < 0 || !std::isfinite(tau) ||
+      !std::isfinite(lambda))
+    return CS_ERR_ARG;
+  cudaStream_t s = p->stream;
+  if (stats) CS_TRY(cudaEventRecord(p->ev0, s));
+  CallArgs a{};
+  a.src = x;
+  a.x = x;
+  a.xtrue = p->xtrue;
+  a.thr = (float)((double)tau * (double)lambda);
+  a.tau = tau;
+  p->launches = 0;
+  CS_TRY(launch_set_args(a, p->ca, s));
+  CS_TRY(launch_scatter_y(y, p->pos, p->m, p->ys, p->status, s));
+  p->launches += 2;
+  p->ista_args = true;
+  p->admm_args = false;
+  int run = 0, conv = 0;
+  if (iters > 0) {
+    CS_TRY(launch_col(COL_LOAD, kparams(p, p->gi, 0), s));
+    p->launches += 1;
+    CS_TRY(solve_loop(p, K_ISTA, iters, &run, &conv, stats != nullptr));
+  }
+  if (stats) {
+    CS_TRY(cudaEventRecord(p->ev1, s));
+    CS_TRY(cudaMemcpyAsync(p->host_status, p->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CS_TRY(cudaEventSynchronize(p->ev1));
+    CS_TRY(cudaStreamSynchronize(s));
+    p->latched |= *p->host_status;
+    fill_stats(p, stats, run, conv, lambda, false);
+    float ms = 0.f;
+    CS_TRY(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+    stats->ms = ms;
+    return latched_status(p);
+  }
+  return CS_OK;
+}
+
+cs_status cs_admm_ex(cs_plan_t p, const float* y, float lambda, const cs_admm_params* prm, int iters, int warm,
+                     float* x, float* z, float* mu, float* nu, float* v, cs_stats* stats) {
+  if (!p || !y || !prm || !z || !mu || !nu || !v || !(lambda >= 0.f) || iters < 0 || !std::isfinite(lambda))
+    return CS_ERR_ARG;
+  if (!(prm->sigma > 0.0) || !(prm->rho > 0.0) || !(prm->tau1 > 0.0) || !(prm->tau2 > 0.0) ||
+      !std::isfinite(prm->sigma) || !std::isfinite(prm->rho) || !std::isfinite(prm->tau1) ||
+      !std::isfinite(prm->tau2))
+    return CS_ERR_ARG;
+  cudaStream_t s = p->stream;
+  if (stats) CS_TRY(cudaEventRecord(p->ev0, s));
+  const size_t nb = p->n * sizeof(float);
+  if (!warm) {
+    CS_TRY(cudaMemsetAsync(v, 0, nb, s));
+    CS_TRY(cudaMemsetAsync(z, 0, nb, s));
+    CS_TRY(cudaMemsetAsync(mu, 0, nb, s));
+    CS_TRY(cudaMemsetAsync(nu, 0, nb, s));
+  }
+  p->launches = 0;
+  if (prm->rho != p->b_rho || prm->sigma != p->b_sigma) {
+    CS_TRY(launch_tab_admm_b(p->abs2, (int)tab_count(p->ga), p->n, prm->rho, prm->sigma, p->tab_admm_b, s));
+    p->launches += 1;
+    p->b_rho = prm->rho;
+    p->b_sigma = prm->sigma;
+  }
+  CallArgs a{};
+  a.x = x;
+  a.z = z;
+  a.mu = mu;
+  a.nu = nu;
+  a.v = v;
+  a.xtrue = p->xtrue;
+  a.thr = (float)((double)lambda / prm->sigma);
+  a.rho = (float)prm->rho;
+  a.sigma = (float)prm->sigma;
+  a.tau1 = (float)prm->tau1;
+  a.tau2 = (float)prm->tau2;
+  a.d_on = (float)(1.0 / (1.0 + prm->rho));
+  a.d_off = (float)(1.0 / prm->rho);
+  CS_TRY(launch_set_args(a, p->ca, s));
+  CS_TRY(launch_scatter_y(y, p->pos, p->m, p->ys, p->status, s));
+  p->launches += 2;
+  p->admm_args = true;
+  p->ista_args = false;
+  int run = 0, conv = 0;
+  if (iters > 0) {
+    CS_TRY(launch_col(COL_ADMM_INIT, kparams(p, p->ga, 0), s));
+    p->launches += 1;
+    CS_TRY(solve_loop(p, K_ADMM, iters, &run, &conv, stats != nullptr));
+  }
+  if (stats) {
+    CS_TRY(cudaEventRecord(p->ev1, s));
+    CS_TRY(cudaMemcpyAsync(p->host_status, p->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CS_TRY(cudaStreamSynchronize(s));
+    p->latched |= *p->host_status;
+    fill_stats(p, stats, run, conv, lambda, true);
+    float ms = 0.f;
+    CS_TRY(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+    stats->ms = ms;
+    return latched_status(p);
+  }
+  return CS_OK;
+}
+
+cs_status cs_profile_pass(cs_plan_t p, int pass_id, int reps) {
+  if (!p || reps < 1 || pass_id < 0 || pass_id > 5) return CS_ERR_ARG;
+  if (pass_id <= 3 && !p->ista_args) return CS_ERR_ARG;
+  if (pass_id >= 4 && !p->admm_args) return CS_ERR_ARG;
+  cudaStream_t s = p->stream;
+  for (int r = 0; r < reps; ++r) {
+    switch (pass_id) {
+      case 0: CS_TRY(launch_mid(MID_FWD, kparams(p, p->gi, 0), s)); break;
+      case 1: CS_TRY(launch_col(COL_RESIDUAL, kparams(p, p->gi, 0), s)); break;
+      case 2: CS_TRY(launch_mid(MID_ADJ, kparams(p, p->gi, 0), s)); break;
+      case 3: CS_TRY(launch_col(COL_ISTA, kparams(p, p->gi, 0), s)); break;
+      case 4: CS_TRY(launch_mid(MID_ADMM, kparams(p, p->ga, 0), s)); break;
+      default: CS_TRY(launch_col(COL_ADMM, kparams(p, p->ga, 0), s)); break;
+    }
+  }
+  return CS_OK;
+}
+
+cs_status cs_admm(cs_plan_t p, const float* y, float lambda, float rho, int iters, float* z, cs_stats* stats) {
+  if (!p || !y || !z || !(rho > 0.f) || !(lambda >= 0.f) || iters < 0) return CS_ERR_ARG;
+  cs_admm_params prm{rho, rho, 1.0, 1.0};
+  // the state of Algorithm 3 lives in plan scratch; only z is returned
+  return cs_admm_ex(p, y, lambda, &prm, iters, 0, nullptr, z, p->dense2, p->dense3, p->dense, stats);
+}
+
+}  // extern "C"

@@ -1,0 +1,316 @@
+// Plan-time and bookkeeping kernels: FP64 spectrum of c, twiddle and spectrum
+// tables, the row mask of Omega, y scatter / gather, deterministic reductions.
+#include "cs_internal.h"
+
+namespace csk {
+
+namespace {
+
+constexpr int AUX_NT = 256;
+
+__global__ void set_args_k(CallArgs a, CallArgs* dst) { *dst = a; }
+
+// Deterministic final sum of per-block partials, slot by slot.
+__global__ void __launch_bounds__(AUX_NT) finalize_k(const double* __restrict__ partials, int nblk,
+                                                     double* __restrict__ stats) {
+  __shared__ double red[AUX_NT];
+  for (int k = 0; k < NSTAT; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += AUX_NT) s += partials[b * NSTAT + k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = AUX_NT / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) stats[k] = red[0];
+    __syncthreads();
+  }
+}
+
+// dst[q] = exp(-2 pi i q / M), evaluated in FP64 (exact rational argument)
+// and rounded once to fp32.
+__global__ void twiddle_k(float2* dst, int count, int64_t M) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  double s, c;
+  sincospi(-2.0 * (double)q / (double)M, &s, &c);
+  dst[q] = make_float2((float)c, (float)s);
+}
+
+__global__ void c_to_complex_k(const double* __restrict__ c, double2* __restrict__ a, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = make_double2(c[i], 0.0);
+}
+
+// One radix-2 Stockham stage of the FP64 plan-time FFT (global memory):
+// butterfly j pairs a[j] and a[j + n/2]; Ls is the current sub-transform length.
+__global__ void fft64_stage_k(const double2* __restrict__ in, double2* __restrict__ out, int64_t n,
+                              int64_t Ls) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t h = n >> 1;
+  if (j >= h) return;
+  const int64_t k = j & (Ls - 1);
+  double s, c;
+  sincospi(-(double)k / (double)Ls, &s, &c);   // exp(-2 pi i k / (2 Ls))
+  const double2 a = in[j], b0 = in[j + h];
+  const double2 b = make_double2(b0.x * c - b0.y * s, b0.x * s + b0.y * c);
+  const int64_t o = ((j - k) << 1) + k;
+  out[o] = make_double2(a.x + b.x, a.y + b.y);
+  out[o + Ls] = make_double2(a.x - b.x, a.y - b.y);
+}
+
+// chat_k of a real vector: bins 0 and n/2 are real by construction.
+__device__ __forceinline__ double2 chat_at(const double2* chat, int64_t n, int64_t k) {
+  double2 v = chat[k];
+  if (k == 0 || k == (n >> 1)) v.y = 0.0;
+  return v;
+}
+
+// Full frequency index of the first element of pair slot t (see the mid pass).
+__device__ __forceinline__ int64_t slot_freq(const Geo& g, int64_t t) {
+  const int64_t units1 = (int64_t)((g.N2 >> 1) - 1) << g.lgN1;
+  if (t < units1) {
+    const int64_t u = (t >> g.lgN1) + 1, q = t & (g.N1 - 1);
+    return u + ((int64_t)q << g.lgN2);
+  }
+  const int64_t q = t - units1;
+  if (q <= (g.N1 >> 1)) return q << g.lgN2;
+  return (g.N2 >> 1) + ((q - (g.N1 >> 1) - 1) << g.lgN2);
+}
+
+// Real-FFT geometry (N = n/2): P = (chat_k + chat_{k+N}) / 2N,
+// Q = (chat_k - chat_{k+N}) / 2N, computed in FP64, rounded once.
+__global__ void tab_ista_k(const double2* __restrict__ chat, Geo g, int64_t n, float4* __restrict__ tab,
+                           int64_t count) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t k = slot_freq(g, t);
+  const double2 a = chat_at(chat, n, k), b = chat_at(chat, n, k + g.N);
+  const double s = 0.5 / (double)g.N;
+  tab[t] = make_float4((float)((a.x + b.x) * s), (float)((a.y + b.y) * s), (float)((a.x - b.x) * s),
+                       (float)((a.y - b.y) * s));
+}
+
+// Complex-n geometry (N = n): chat_k in fp32 and |chat_k|^2 in FP64.
+__global__ void tab_admm_k(const double2* __restrict__ chat, Geo g, int64_t n, float2* __restrict__ tabc,
+                           double* __restrict__ abs2, int64_t count) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t k = slot_freq(g, t);
+  const double2 a = chat_at(chat, n, k);
+  tabc[t] = make_float2((float)a.x, (float)a.y);
+  abs2[t] = a.x * a.x + a.y * a.y;
+}
+
+// Spectrum of B = (rho C^T C + sigma I)^-1 (Algorithm 3, initial inversion),
+// with the 1/n of the inverse FFT folded in; FP64, rounded once.
+__global__ void tab_admm_b_k(const double* __restrict__ abs2, int64_t count, int64_t n, double rho,
+                             double sigma, float* __restrict__ tabb) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  tabb[t] = (float)(1.0 / ((double)n * (rho * abs2[t] + sigma)));
+}
+
+__global__ void build_mask_k(const int64_t* __restrict__ rows, int64_t m, int64_t n, uint32_t* mask,
+                             int* status) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int64_t r = rows[i];
+  if (r < 0 || r >= n) { atomicOr(status, STS_BAD_ROW); return; }
+  const uint32_t bit = 1u << (r & 31);
+  const uint32_t old = atomicOr(mask + (r >> 5), bit);
+  if (old & bit) atomicOr(status, STS_DUP_ROW);
+}
+
+// Exclusive prefix count of set bits per 32-bit word, one CTA.
+__global__ void __launch_bounds__(1024) prefix_k(const uint32_t* __restrict__ mask, int64_t words,
+                                                 uint32_t* __restrict__ prefix) {
+  __shared__ uint32_t part[1024];
+  const int64_t per = (words + 1023) / 1024;
+  const int64_t lo = threadIdx.x * per, hi = min(words, lo + per);
+  uint32_t s = 0;
+  for (int64_t w = lo; w < hi; ++w) s += __popc(mask[w]);
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int i = 0; i < 1024; ++i) { const uint32_t v = part[i]; part[i] = acc; acc += v; }
+  }
+  __syncthreads();
+  uint32_t acc = part[threadIdx.x];
+  for (int64_t w = lo; w < hi; ++w) { prefix[w] = acc; acc += __popc(mask[w]); }
+}
+
+__global__ void row_pos_k(const int64_t* __restrict__ rows, int64_t m, const uint32_t* __restrict__ mask,
+                          const uint32_t* __restrict__ prefix, int32_t* __restrict__ pos,
+                          int32_t* __restrict__ rows32) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int64_t r = rows[i];
+  const uint32_t w = mask[r >> 5];
+  pos[i] = (int32_t)(prefix[r >> 5] + __popc(w & ((1u << (r & 31)) - 1u)));
+  rows32[i] = (int32_t)r;
+}
+
+__global__ void scatter_y_k(const float* __restrict__ y, const int32_t* __restrict__ pos, int64_t m,
+                            float* __restrict__ ys, int* status) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const float v = y[i];
+  if (!isfinite(v)) atomicOr(status, STS_NONFINITE);
+  ys[pos[i]] = v;
+}
+
+__global__ void gather_rows_k(const float* __restrict__ dense, const int32_t* __restrict__ rows32, int64_t m,
+                              float* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m) y[i] = dense[rows32[i]];
+}
+
+__global__ void scatter_rows_k(const float* __restrict__ r, const int32_t* __restrict__ rows32, int64_t m,
+                               float* __restrict__ dense) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m) dense[rows32[i]] = r[i];
+}
+
+constexpr int NORM_BLOCKS = 256;
+
+__global__ void __launch_bounds__(AUX_NT) norm2_part_k(const float* __restrict__ x, int64_t n,
+                                                       double* __restrict__ partials) {
+  __shared__ double red[AUX_NT];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)AUX_NT + threadIdx.x; i < n; i += (int64_t)NORM_BLOCKS * AUX_NT) {
+    const double v = x[i];
+    s += v * v;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = AUX_NT / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void norm2_final_k(const double* __restrict__ partials, double* out) {
+  __shared__ double red[NORM_BLOCKS];
+  red[threadIdx.x] = partials[threadIdx.x];
+  __syncthreads();
+  for (int w = NORM_BLOCKS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// Fixed start vector for the power iteration: a 32-bit integer hash of the
+// index mapped to [-1, 1).
+__global__ void power_init_k(float* u, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t h = (uint32_t)i * 2654435761u + 0x9e3779b9u;
+  h ^= h >> 16; h *= 0x85ebca6bu; h ^= h >> 13; h *= 0xc2b2ae35u; h ^= h >> 16;
+  u[i] = (float)((double)h * (2.0 / 4294967296.0) - 1.0);
+}
+
+inline unsigned blocks_for(int64_t count) { return (unsigned)((count + AUX_NT - 1) / AUX_NT); }
+
+}  // namespace
+
+cudaError_t launch_set_args(const CallArgs& a, CallArgs* dst, cudaStream_t s) {
+  set_args_k<<<1, 1, 0, s>>>(a, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* partials, int nblk, double* stats, cudaStream_t s) {
+  finalize_k<<<1, AUX_NT, 0, s>>>(partials, nblk, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_twiddle(float2* dst, int count, int64_t M, cudaStream_t s) {
+  twiddle_k<<<blocks_for(count), AUX_NT, 0, s>>>(dst, count, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft64(const double* c, double2* a, double2* b, int64_t n, double2** out,
+                         cudaStream_t s) {
+  c_to_complex_k<<<blocks_for(n), AUX_NT, 0, s>>>(c, a, n);
+  double2* in = a;
+  double2* o = b;
+  for (int64_t Ls = 1; Ls < n; Ls <<= 1) {
+    fft64_stage_k<<<blocks_for(n >> 1), AUX_NT, 0, s>>>(in, o, n, Ls);
+    double2* t = in; in = o; o = t;
+  }
+  *out = in;
+  return cudaGetLastError();
+}
+
+static int64_t tab_count(const Geo& g) { return ((int64_t)(g.N2 >> 1) << g.lgN1) + 1; }
+
+cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tab, cudaStream_t s) {
+  const int64_t cnt = tab_count(g);
+  tab_ista_k<<<blocks_for(cnt), AUX_NT, 0, s>>>(chat, g, n, tab, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tab_admm(const double2* chat, const Geo& g, int64_t n, float2* tabc, double* abs2,
+                            cudaStream_t s) {
+  const int64_t cnt = tab_count(g);
+  tab_admm_k<<<blocks_for(cnt), AUX_NT, 0, s>>>(chat, g, n, tabc, abs2, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tab_admm_b(const double* abs2, int count, int64_t n, double rho, double sigma,
+                              float* tabb, cudaStream_t s) {
+  tab_admm_b_k<<<blocks_for(count), AUX_NT, 0, s>>>(abs2, count, n, rho, sigma, tabb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_mask(const int64_t* rows, int64_t m, int64_t n, uint32_t* mask, int* status,
+                              cudaStream_t s) {
+  build_mask_k<<<blocks_for(m), AUX_NT, 0, s>>>(rows, m, n, mask, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prefix(const uint32_t* mask, int64_t words, uint32_t* prefix, cudaStream_t s) {
+  prefix_k<<<1, 1024, 0, s>>>(mask, words, prefix);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_pos(const int64_t* rows, int64_t m, const uint32_t* mask, const uint32_t* prefix,
+                           int32_t* pos, int32_t* rows32, cudaStream_t s) {
+  row_pos_k<<<blocks_for(m), AUX_NT, 0, s>>>(rows, m, mask, prefix, pos, rows32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_y(const float* y, const int32_t* pos, int64_t m, float* ys, int* status,
+                             cudaStream_t s) {
+  scatter_y_k<<<blocks_for(m), AUX_NT, 0, s>>>(y, pos, m, ys, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const float* dense, const int32_t* rows32, int64_t m, float* y,
+                               cudaStream_t s) {
+  gather_rows_k<<<blocks_for(m), AUX_NT, 0, s>>>(dense, rows32, m, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_rows(const float* r, const int32_t* rows32, int64_t m, float* dense,
+                                cudaStream_t s) {
+  scatter_rows_k<<<blocks_for(m), AUX_NT, 0, s>>>(r, rows32, m, dense);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm2(const float* x, int64_t n, double* partials, double* out, cudaStream_t s) {
+  norm2_part_k<<<NORM_BLOCKS, AUX_NT, 0, s>>>(x, n, partials);
+  norm2_final_k<<<1, NORM_BLOCKS, 0, s>>>(partials, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_power_init(float* u, int64_t n, cudaStream_t s) {
+  power_init_k<<<blocks_for(n), AUX_NT, 0, s>>>(u, n);
+  return cudaGetLastError();
+}
+
+}  // namespace csk

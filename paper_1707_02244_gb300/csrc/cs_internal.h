@@ -1,0 +1,133 @@
+// Internal declarations shared by the host runtime and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace csk {
+
+// Four-step geometry of one complex FFT of length N = N1 * N2, stored as an
+// N2 x N1 row-major array (element p = j1 + N1 * j2).
+//   column pass: length-N2 FFTs down the columns, G columns per CTA
+//   mid pass:    length-N1 FFTs along the rows, U row pairs per CTA; row
+//                pair unit u holds rows (u, N2 - u) for u >= 1 and rows
+//                (0, N2/2) for u = 0, so every frequency k meets its mirror
+//                N - k inside one CTA.
+struct Geo {
+  int N, lgN, N1, lgN1, N2, lgN2;
+  int G, lgG, col_ctas;
+  int U, lgU, mid_ctas;
+  const float2* tw1;   // exp(-2 pi i q / (2 N1)), q < 2 N1
+  const float2* tw2;   // exp(-2 pi i q / N2),     q < N2
+  const float2* twl;   // exp(-2 pi i q / N),      q < N1
+  const float2* twr;   // exp(-2 pi i q / (2 N)),  q < N2
+};
+
+constexpr int NSTAT = 8;
+
+// Statistic slots (partials[block * NSTAT + slot]).
+enum : int {
+  ST_ERR2 = 0,   // ||x - x*||^2           (ISTA: x_t, ADMM: z_t)
+  ST_DX2 = 1,    // ISTA ||x_t - x_{t-1}||^2, ADMM ||x_t - z_t||^2
+  ST_X2 = 2,     // ||x_t||^2 (ADMM ||z_t||^2)
+  ST_L1 = 3,     // ISTA ||x_{t-1}||_1, ADMM ||z_t||_1
+  ST_R2 = 4,     // ||y - A x||^2 (ISTA at x_{t-1}, ADMM at x_t)
+  ST_NONFIN = 5  // count of non-finite iterate values
+};
+
+// Plan-constant device pointers, passed by value to every pass kernel.
+struct PlanPtrs {
+  float2* W;                 // exchange buffer, complex[n]
+  const uint32_t* mask;      // bit r set iff row r is in Omega, [n/32]
+  const uint32_t* prefix;    // set bits before word w, [n/32]
+  const float* ys;           // y in ascending-row order, [m]
+  double* partials;          // [max_ctas * NSTAT]
+  double* stats;             // [NSTAT] finalised sums
+  const float4* tab_ista;    // (P, Q) per pair slot, real-FFT geometry
+  const float2* tab_admm_c;  // chat_k per pair slot, complex-n geometry
+  const float* tab_admm_b;   // 1 / (n (rho |chat_k|^2 + sigma)) per pair slot
+  int* status;               // device status word
+};
+
+// Per-call arguments, resident in device memory and written by a one-thread
+// kernel at the start of each call (kernel parameters are captured when the
+// launch is enqueued, so this is safe while earlier work is in flight).
+struct CallArgs {
+  const float* src;     // load source (x, scattered r, power vector)
+  float* dst;           // store target
+  float* aux;           // power iteration: normalised u
+  const float* xtrue;   // monitor ground truth or null
+  float* x;             // ISTA iterate / ADMM x output (may be null)
+  float* z;
+  float* mu;
+  float* nu;
+  float* v;
+  float thr;            // ISTA tau*lambda, ADMM lambda/sigma
+  float tau;            // ISTA step
+  float rho, sigma, tau1, tau2, d_on, d_off;
+};
+
+struct KParams {
+  Geo geo;
+  PlanPtrs pp;
+  const CallArgs* ca;
+  int flags;
+};
+
+enum : int { FL_STATS = 1, FL_WRITE_STATE = 2, FL_POWER_SCALE = 4 };
+
+// Column-pass epilogues and mid-pass spectrum operators.
+enum ColKind : int {
+  COL_LOAD = 0,        // forward FFT of src (real-FFT geometry: src float[2N])
+  COL_LOAD_SCALED,     // same, times 1/sqrt(stats[ST_X2]); copies it to aux
+  COL_STORE,           // inverse FFT, store to dst
+  COL_MASK,            // inverse, keep rows of Omega, forward
+  COL_RESIDUAL,        // inverse, r = M (y - Cx), forward
+  COL_ISTA,            // inverse, x <- eta(x + tau g), forward
+  COL_ISTA_LAST,       // same without the forward FFT
+  COL_POWER_OUT,       // inverse, w -> dst, stats <u, w>, ||w||^2
+  COL_ADMM_INIT,       // complex-n geometry: forward FFT of (v) + i (z - nu)
+  COL_ADMM,            // inverse, Algorithm 3 elementwise steps, forward
+  COL_ADMM_LAST        // same without the forward FFT
+};
+enum MidKind : int { MID_FWD = 0, MID_ADJ, MID_ADMM };
+
+// Launchers (cs_passes.cu).  Return cudaGetLastError() of the launch.
+cudaError_t launch_col(ColKind kind, const KParams& kp, cudaStream_t s);
+cudaError_t launch_mid(MidKind kind, const KParams& kp, cudaStream_t s);
+size_t pass_smem_bytes();
+cudaError_t init_pass_kernels();
+
+// Small kernels (cs_aux.cu).
+cudaError_t launch_set_args(const CallArgs& a, CallArgs* dst, cudaStream_t s);
+cudaError_t launch_finalize(const double* partials, int nblk, double* stats, cudaStream_t s);
+cudaError_t launch_twiddle(float2* dst, int count, int64_t M, cudaStream_t s);
+cudaError_t launch_fft64(const double* c, double2* a, double2* b, int64_t n, double2** out,
+                         cudaStream_t s);
+cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tab,
+                            cudaStream_t s);
+cudaError_t launch_tab_admm(const double2* chat, const Geo& g, int64_t n, float2* tabc,
+                            double* abs2, cudaStream_t s);
+cudaError_t launch_tab_admm_b(const double* abs2, int count, int64_t n, double rho,
+                              double sigma, float* tabb, cudaStream_t s);
+cudaError_t launch_build_mask(const int64_t* rows, int64_t m, int64_t n, uint32_t* mask,
+                              int* status, cudaStream_t s);
+cudaError_t launch_prefix(const uint32_t* mask, int64_t words, uint32_t* prefix,
+                          cudaStream_t s);
+cudaError_t launch_row_pos(const int64_t* rows, int64_t m, const uint32_t* mask,
+                           const uint32_t* prefix, int32_t* pos, int32_t* rows32,
+                           cudaStream_t s);
+cudaError_t launch_scatter_y(const float* y, const int32_t* pos, int64_t m, float* ys,
+                             int* status, cudaStream_t s);
+cudaError_t launch_gather_rows(const float* dense, const int32_t* rows32, int64_t m,
+                               float* y, cudaStream_t s);
+cudaError_t launch_scatter_rows(const float* r, const int32_t* rows32, int64_t m,
+                                float* dense, cudaStream_t s);
+cudaError_t launch_norm2(const float* x, int64_t n, double* partials, double* out,
+                         cudaStream_t s);
+cudaError_t launch_power_init(float* u, int64_t n, cudaStream_t s);
+
+// Device status bits.
+enum : int { STS_NONFINITE = 1, STS_TIMEOUT = 2, STS_BAD_ROW = 4, STS_DUP_ROW = 8 };
+
+}  // namespace csk

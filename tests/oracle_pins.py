@@ -69,6 +69,10 @@ def check_fft_products_match_dense(O):
         assert np.allclose(O.forward_fft(chat, rows, x), A @ x, rtol=0, atol=1e-11 * n)
         assert np.allclose(O.adjoint_fft(chat, rows, r), A.T @ r, rtol=0, atol=1e-11 * n)
         assert np.allclose(O.forward_dense(c, rows, x), A @ x, atol=1e-12)
+        idx = np.arange(0, m, 3)
+        assert np.allclose(O.forward_sampled(c, rows, x, idx), (A @ x)[idx], atol=1e-12)
+        jdx = np.arange(0, n, 5)
+        assert np.allclose(O.adjoint_sampled(c, rows, r, jdx), (A.T @ r)[jdx], atol=1e-12)
 
 
 def check_adjoint_identity(O):

@@ -1,0 +1,81 @@
+"""C-ABI contract checks that need no GPU: the library loads, exports every
+entry point include/cs.h declares, and rejects bad arguments before touching
+the device."""
+import ctypes
+import pathlib
+import re
+
+import numpy as np
+import pytest
+
+ROOT = pathlib.Path(__file__).resolve().parents[1]
+HEADER = ROOT / "include" / "cs.h"
+
+
+def _declared():
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cs_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def cs():
+    lib = ROOT / "paper_1707_02244_gb300" / "libcsgb.so"
+    if not lib.exists():
+        pytest.skip("libcsgb.so not built (run __graft_entry__.build())")
+    import paper_1707_02244_gb300 as cs
+    return cs
+
+
+def test_header_declares_expected_calls():
+    names = _declared()
+    for n in ("cs_plan", "cs_plan_destroy", "cs_forward", "cs_adjoint", "cs_ista", "cs_admm",
+              "cs_admm_ex", "cs_opnorm2", "cs_set_monitor", "cs_status_sync"):
+        assert n in names, n
+
+
+def test_every_declared_symbol_is_exported(cs):
+    lib = ctypes.CDLL(str(cs.LIB_PATH))
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(cs.EXPORTS) <= set(_declared())
+
+
+def test_version_and_strings(cs):
+    assert cs.cs_version() >= 100
+    assert cs.status_string(0) == "CS_OK"
+    assert cs.status_string(1) == "CS_ERR_ARG"
+    assert cs.status_string(6) == "CS_ERR_UNSUPPORTED"
+
+
+def test_plan_rejects_bad_arguments_without_device(cs):
+    h = ctypes.c_void_p()
+    rows = np.arange(8, dtype=np.int64)
+    c = np.zeros(64)
+    # null out / rows / c
+    assert cs.raw_call("cs_plan", None, 64, 8, rows.ctypes.data, c.ctypes.data, None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_plan", ctypes.byref(h), 64, 8, None, c.ctypes.data, None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_plan", ctypes.byref(h), 64, 8, rows.ctypes.data, None, None) == cs.CS_ERR_ARG
+    # m out of range
+    assert cs.raw_call("cs_plan", ctypes.byref(h), 64, 0, rows.ctypes.data, c.ctypes.data, None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_plan", ctypes.byref(h), 64, 65, rows.ctypes.data, c.ctypes.data, None) == cs.CS_ERR_ARG
+    # unsupported n: not a power of two, too small, too large
+    for n in (100, 32, 1 << 23):
+        cn = np.zeros(min(n, 128))
+        assert cs.raw_call("cs_plan", ctypes.byref(h), n, 8, rows.ctypes.data, cn.ctypes.data,
+                           None) == cs.CS_ERR_UNSUPPORTED, n
+
+
+def test_null_plan_is_an_argument_error(cs):
+    st = cs.CsStats()
+    assert cs.raw_call("cs_plan_destroy", None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_forward", None, None, None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_adjoint", None, None, None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_ista", None, None, ctypes.c_float(0.1), ctypes.c_float(1.0), 1, None,
+                       ctypes.byref(st)) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_admm", None, None, ctypes.c_float(0.1), ctypes.c_float(1.0), 1, None,
+                       None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_status_sync", None) == cs.CS_ERR_ARG
+    L = ctypes.c_double()
+    assert cs.raw_call("cs_opnorm2", None, 10, ctypes.byref(L)) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_set_monitor", None, None, ctypes.c_double(0.0), 10) == cs.CS_ERR_ARG

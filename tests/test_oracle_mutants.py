@@ -26,9 +26,11 @@ def _mut_reverse_circulant(c):
 
 
 def _mut_conj_fft(chat, x, transpose=False):
-    xh = np.fft.fft(np.asarray(x, dtype=np.float64))
-    h = np.conj(chat) if transpose else chat
-    return np.fft.ifft(h * xh).real
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    h = chat[: n // 2 + 1]
+    h = np.conj(h) if transpose else h
+    return np.fft.irfft(h * np.fft.rfft(x), n)
 
 
 def _mut_threshold_hard(x, gamma):

@@ -30,6 +30,7 @@ struct cs_plan_s {
   int* status = nullptr;
   CallArgs* ca = nullptr;
   float4* tab_ista = nullptr;
+  float2* tab_ista_b = nullptr;
   float2* tab_admm_c = nullptr;
   float* tab_admm_b = nullptr;
   double* abs2 = nullptr;
@@ -64,21 +65,31 @@ int ilog2(int64_t v) {
 }
 
 void make_geo(Geo& g, int lgN) {
-  constexpr int lgTILE = 13;   // TILE = 8192
   g.lgN = lgN;
   g.N = 1 << lgN;
   g.lgN2 = lgN / 2 < 10 ? lgN / 2 : 10;
   g.N2 = 1 << g.lgN2;
   g.lgN1 = lgN - g.lgN2;
   g.N1 = 1 << g.lgN1;
-  g.lgG = (lgTILE - g.lgN2) < g.lgN1 ? (lgTILE - g.lgN2) : g.lgN1;
+  // column pass: 4096-value tiles (256 threads), G = 4096 / N2 >= 4 columns
+  const int lgCol = 12;
+  g.lgG = (lgCol - g.lgN2) < g.lgN1 ? (lgCol - g.lgN2) : g.lgN1;
   g.G = 1 << g.lgG;
   g.col_ctas = g.N1 >> g.lgG;
-  const int lgUmax = lgTILE - 1 - g.lgN1;
+  // mid pass: 4096-value tiles when a row pair fits, else 8192 (512 threads)
+  const int lgMid = g.lgN1 <= 11 ? 12 : 13;
+  g.tile = 1 << lgMid;
+  const int lgUmax = lgMid - 1 - g.lgN1;
   const int lgUnits = g.lgN2 - 1;
   g.lgU = lgUmax < lgUnits ? lgUmax : lgUnits;
   g.U = 1 << g.lgU;
   g.mid_ctas = (g.N2 >> 1) >> g.lgU;
+}
+
+// Geometry invariants the pass kernels rely on (checked for every plan).
+bool geo_ok(const Geo& g) {
+  return g.N1 >= g.N2 && g.N2 >= 2 && g.G >= 2 && g.col_ctas >= 1 && g.mid_ctas >= 1 &&
+         2 * g.U <= 64 && (2 * g.U) * g.N1 <= g.tile && (g.G << g.lgN2) <= 4096;
 }
 
 int64_t tab_count(const Geo& g) { return ((int64_t)(g.N2 >> 1) << g.lgN1) + 1; }
@@ -104,7 +115,7 @@ void free_plan(cs_plan_s* p) {
   if (!p) return;
   for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
   void* bufs[] = {p->W, p->mask, p->prefix, p->pos, p->rows32, p->ys, p->partials, p->stats, p->status,
-                  p->ca, p->tab_ista, p->tab_admm_c, p->tab_admm_b, p->abs2, p->twi, p->twa,
+                  p->ca, p->tab_ista, p->tab_ista_b, p->tab_admm_c, p->tab_admm_b, p->abs2, p->twi, p->twa,
                   p->dense, p->dense2, p->dense3};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -126,6 +137,7 @@ KParams kparams(const cs_plan_s* p, const Geo& g, int flags) {
   k.pp.partials = p->partials;
   k.pp.stats = p->stats;
   k.pp.tab_ista = p->tab_ista;
+  k.pp.tab_ista_b = p->tab_ista_b;
   k.pp.tab_admm_c = p->tab_admm_c;
   k.pp.tab_admm_b = p->tab_admm_b;
   k.pp.status = p->status;
@@ -135,23 +147,33 @@ KParams kparams(const cs_plan_s* p, const Geo& g, int flags) {
 }
 
 cudaError_t make_tables(Geo& g, float2* base, cudaStream_t s) {
-  // tw1 [2 N1] | tw2 [N2] | twl [N1] | twr [N2]
+  // tw1 [2 N1] | tw2 [N2] | twl [N1] | twr [N2] | tw1h [N1] | tws1 [N1] | tws2 [N2]
+  // (every block starts at an even index: 16-byte aligned)
   float2* tw1 = base;
   float2* tw2 = tw1 + 2 * g.N1;
   float2* twl = tw2 + g.N2;
   float2* twr = twl + g.N1;
+  float2* tw1h = twr + g.N2;
+  float2* tws1 = tw1h + g.N1;
+  float2* tws2 = tws1 + g.N1;
   cudaError_t e = launch_twiddle(tw1, 2 * g.N1, 2 * (int64_t)g.N1, s);
   if (e == cudaSuccess) e = launch_twiddle(tw2, g.N2, g.N2, s);
   if (e == cudaSuccess) e = launch_twiddle(twl, g.N1, g.N, s);
   if (e == cudaSuccess) e = launch_twiddle(twr, g.N2, 2 * (int64_t)g.N, s);
+  if (e == cudaSuccess) e = launch_twiddle(tw1h, g.N1, g.N1, s);
+  if (e == cudaSuccess) e = launch_stage_tw(tws1, g.lgN1, stage_tw_count(g.lgN1), s);
+  if (e == cudaSuccess) e = launch_stage_tw(tws2, g.lgN2, stage_tw_count(g.lgN2), s);
   g.tw1 = tw1;
   g.tw2 = tw2;
   g.twl = twl;
   g.twr = twr;
+  g.tw1h = tw1h;
+  g.tws1 = tws1;
+  g.tws2 = tws2;
   return e;
 }
 
-size_t twiddle_count(const Geo& g) { return 3 * (size_t)g.N1 + 2 * (size_t)g.N2; }
+size_t twiddle_count(const Geo& g) { return 5 * (size_t)g.N1 + 3 * (size_t)g.N2; }
 
 // Read the device status word and the finalised stats into pinned memory.
 cudaError_t read_back(cs_plan_s* p) {
@@ -314,6 +336,10 @@ cs_status cs_plan(cs_plan_t* out, int64_t n, int64_t m, const int64_t* rows, con
   const int lgn = ilog2(n);
   make_geo(p->gi, lgn - 1);
   make_geo(p->ga, lgn);
+  if (!geo_ok(p->gi) || !geo_ok(p->ga)) {
+    delete p;
+    return CS_ERR_UNSUPPORTED;
+  }
 
   int64_t* d_rows = nullptr;
   double* d_c = nullptr;
@@ -352,6 +378,7 @@ cs_status cs_plan(cs_plan_t* out, int64_t n, int64_t m, const int64_t* rows, con
   CS_PLAN_TRY(dalloc(&p->status, 1));
   CS_PLAN_TRY(dalloc(&p->ca, 1));
   CS_PLAN_TRY(dalloc(&p->tab_ista, tab_count(p->gi)));
+  CS_PLAN_TRY(dalloc(&p->tab_ista_b, tab_count(p->gi)));
   CS_PLAN_TRY(dalloc(&p->tab_admm_c, tab_count(p->ga)));
   CS_PLAN_TRY(dalloc(&p->tab_admm_b, tab_count(p->ga)));
   CS_PLAN_TRY(dalloc(&p->abs2, tab_count(p->ga)));
@@ -377,7 +404,7 @@ cs_status cs_plan(cs_plan_t* out, int64_t n, int64_t m, const int64_t* rows, con
   CS_PLAN_TRY(make_tables(p->ga, p->twa, s));
   double2* chat = nullptr;
   CS_PLAN_TRY(launch_fft64(d_c, fa, fb, n, &chat, s));
-  CS_PLAN_TRY(launch_tab_ista(chat, p->gi, n, p->tab_ista, s));
+  CS_PLAN_TRY(launch_tab_ista(chat, p->gi, n, p->tab_ista, p->tab_ista_b, s));
   CS_PLAN_TRY(launch_tab_admm(chat, p->ga, n, p->tab_admm_c, p->abs2, s));
   CS_PLAN_TRY(launch_tab_admm_b(p->abs2, (int)tab_count(p->ga), n, 1.0, 1.0, p->tab_admm_b, s));
   p->b_rho = 1.0;

@@ -38,6 +38,27 @@ __global__ void twiddle_k(float2* dst, int count, int64_t M) {
   dst[q] = make_float2((float)c, (float)s);
 }
 
+// Stage-major twiddle table of a length-L FFT (see stockham_stage): stage
+// with span Ls and radix R holds w_{Ls R}^(r k) at (r - 1) Ls + k.
+__global__ void stage_tw_k(float2* dst, int lgL, int count) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int lgLs = 4;
+  while (true) {
+    const int lgR = (lgL - lgLs) >= 4 ? 4 : (lgL - lgLs);
+    const int sz = ((1 << lgR) - 1) << lgLs;
+    if (t < sz) {
+      const int r = (t >> lgLs) + 1, k = t & ((1 << lgLs) - 1);
+      double sn, cs;
+      sincospi(-2.0 * (double)(r * k) / (double)(1 << (lgLs + lgR)), &sn, &cs);
+      dst[blockIdx.x * blockDim.x + threadIdx.x] = make_float2((float)cs, (float)sn);
+      return;
+    }
+    t -= sz;
+    lgLs += lgR;
+  }
+}
+
 __global__ void c_to_complex_k(const double* __restrict__ c, double2* __restrict__ a, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) a[i] = make_double2(c[i], 0.0);
@@ -79,17 +100,23 @@ __device__ __forceinline__ int64_t slot_freq(const Geo& g, int64_t t) {
   return (g.N2 >> 1) + ((q - (g.N1 >> 1) - 1) << g.lgN2);
 }
 
-// Real-FFT geometry (N = n/2): P = (chat_k + chat_{k+N}) / 2N,
-// Q = (chat_k - chat_{k+N}) / 2N, computed in FP64, rounded once.
-__global__ void tab_ista_k(const double2* __restrict__ chat, Geo g, int64_t n, float4* __restrict__ tab,
-                           int64_t count) {
+// Real-FFT geometry (N = n/2), pair (k, N - k), spectrum H = chat (the C^T
+// product): P = (H_k + H_{k+N}) / 2N, Q = (H_k - H_{k+N}) / 2N, theta = pi k / N,
+//   a = P - Q sin(theta),  a' = conj(P + Q sin(theta)),  b = i Q cos(theta),
+// all in FP64, rounded once: tabA = (a, a'), tabB = b.
+__global__ void tab_ista_k(const double2* __restrict__ chat, Geo g, int64_t n, float4* __restrict__ tabA,
+                           float2* __restrict__ tabB, int64_t count) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count) return;
   const int64_t k = slot_freq(g, t);
   const double2 a = chat_at(chat, n, k), b = chat_at(chat, n, k + g.N);
   const double s = 0.5 / (double)g.N;
-  tab[t] = make_float4((float)((a.x + b.x) * s), (float)((a.y + b.y) * s), (float)((a.x - b.x) * s),
-                       (float)((a.y - b.y) * s));
+  const double Px = (a.x + b.x) * s, Py = (a.y + b.y) * s, Qx = (a.x - b.x) * s, Qy = (a.y - b.y) * s;
+  double sn, cs;
+  sincospi((double)k / (double)g.N, &sn, &cs);
+  tabA[t] = make_float4((float)(Px - Qx * sn), (float)(Py - Qy * sn), (float)(Px + Qx * sn),
+                        (float)(-(Py + Qy * sn)));
+  tabB[t] = make_float2((float)(-Qy * cs), (float)(Qx * cs));
 }
 
 // Complex-n geometry (N = n): chat_k in fp32 and |chat_k|^2 in FP64.
@@ -248,9 +275,15 @@ cudaError_t launch_fft64(const double* c, double2* a, double2* b, int64_t n, dou
 
 static int64_t tab_count(const Geo& g) { return ((int64_t)(g.N2 >> 1) << g.lgN1) + 1; }
 
-cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tab, cudaStream_t s) {
+cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tabA, float2* tabB,
+                            cudaStream_t s) {
   const int64_t cnt = tab_count(g);
-  tab_ista_k<<<blocks_for(cnt), AUX_NT, 0, s>>>(chat, g, n, tab, cnt);
+  tab_ista_k<<<blocks_for(cnt), AUX_NT, 0, s>>>(chat, g, n, tabA, tabB, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_tw(float2* dst, int lgL, int count, cudaStream_t s) {
+  if (count > 0) stage_tw_k<<<blocks_for(count), AUX_NT, 0, s>>>(dst, lgL, count);
   return cudaGetLastError();
 }
 

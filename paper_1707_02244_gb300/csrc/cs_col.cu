@@ -1,0 +1,159 @@
+// Column pass of the fused FFT iteration: inverse length-N2 FFTs down G
+// columns of the N2 x N1 exchange array, the method's elementwise step
+// (residual on the kept rows, soft threshold, ADMM updates) as the hook of
+// the last inverse stage, then the forward FFTs of the next product.
+#include "cs_passes.cuh"
+
+namespace csk {
+
+namespace {
+
+// ---------------------------------------------------------------- column pass
+
+// The column pass always uses 4096-value tiles (N2 <= 1024 gives G >= 4
+// columns), 4 CTAs per SM.
+constexpr int COL_TILE = 4096;
+constexpr int COL_MINB = 4;
+
+// Epilogue as the post hook of the inverse column FFT: runs on each value as
+// the last stage produces it, so the elementwise step costs no extra pass
+// over shared memory.
+template <int KIND>
+struct EpiHook {
+  static constexpr bool kPre = false, kPost = true;
+  const KParams& kp;
+  const CallArgs& a;
+  int col0, lgN1;
+  Acc& acc;
+  __device__ __forceinline__ void begin(int, int) {}
+  __device__ __forceinline__ float2 pre(int, int, int, int, float2 v) const { return v; }
+  __device__ __forceinline__ float2 post(int vec, int j, int r, int lgLR, float2 v) {
+    return Epi<KIND>::apply(kp, a, v, col0 + vec + ((j + (r << lgLR)) << lgN1), acc);
+  }
+};
+
+// SHAPE 0: any geometry (shape read at run time); SHAPE 1: N2 = 1024 and
+// G = 4 columns, the geometry of every N >= 2^20, fixed at compile time.
+template <int SHAPE> struct ColShape;
+template <> struct ColShape<0> {
+  using Lay = DynLayout;
+  __device__ static Lay lay(const Geo& g) { return Lay{g.lgN2, g.lgG, true}; }
+  __device__ static int lgG(const Geo& g) { return g.lgG; }
+  __device__ static int lgN2(const Geo& g) { return g.lgN2; }
+};
+template <> struct ColShape<1> {
+  using Lay = StaticLayout<10, 2, true>;
+  __device__ static Lay lay(const Geo&) { return Lay{}; }
+  __device__ static constexpr int lgG(const Geo&) { return 2; }
+  __device__ static constexpr int lgN2(const Geo&) { return 10; }
+};
+
+template <int KIND, int SHAPE>
+__global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB) col_kernel(const KParams kp) {
+  constexpr int TILE = COL_TILE;
+  constexpr int NT = Cfg<TILE>::NT;
+  constexpr int NLD = Cfg<TILE>::NLD;
+  using E = Epi<KIND>;
+  using S = ColShape<SHAPE>;
+  extern __shared__ float2 sm[];
+  const Geo& g = kp.geo;
+  const CallArgs a = *kp.ca;
+  const int lgG = S::lgG(g), lgN2 = S::lgN2(g);
+  const int G = 1 << lgG;
+  const int col0 = blockIdx.x << lgG;
+  const int tot = G << lgN2;
+  const auto lay = S::lay(g);
+  constexpr bool TWS = SHAPE != 0;   // static shape: stage-major twiddles in shared memory
+  constexpr int TW_N = TWS ? stage_tw_count(10) : 2;
+  __shared__ __align__(16) float2 tws[TW_N];
+  const float2* tw = TWS ? tws : g.tw2;
+  if (TWS) copy_table<NT>(tws, g.tws2, TW_N);
+  float2* __restrict__ W = kp.pp.W;
+  Acc acc;
+  acc.zero();
+
+  if (E::kRead) {
+    float4 buf[NLD];
+#pragma unroll
+    for (int i = 0; i < NLD; ++i) {
+      const int e = 2 * (threadIdx.x + i * NT);
+      if (e < tot) {
+        const int j2 = e >> lgG, c = e & (G - 1);
+        buf[i] = __ldcg(reinterpret_cast<const float4*>(W + col0 + c + ((size_t)j2 << g.lgN1)));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NLD; ++i) {
+      const int e = 2 * (threadIdx.x + i * NT);
+      if (e < tot) {
+        sm[pad(e)] = make_float2(buf[i].x, buf[i].y);
+        sm[pad(e + 1)] = make_float2(buf[i].z, buf[i].w);
+      }
+    }
+    __syncthreads();
+    EpiHook<KIND> hook{kp, a, col0, g.lgN1, acc};
+    tile_fft<+1, TILE, NT, TWS>(sm, lay, tw, lgN2, hook);
+  } else {
+    for (int e = threadIdx.x; e < tot; e += NT) {
+      const int j2 = e >> lgG, c = e & (G - 1);
+      sm[pad(e)] = E::apply(kp, a, make_float2(0.f, 0.f), col0 + c + (j2 << g.lgN1), acc);
+    }
+    __syncthreads();
+  }
+  if (kp.flags & FL_STATS) {
+    constexpr int kSlots =
+        KIND == COL_RESIDUAL ? (1 << ST_R2)
+        : KIND == COL_POWER_OUT ? ((1 << ST_DX2) | (1 << ST_X2))
+        : (KIND == COL_ISTA || KIND == COL_ISTA_LAST)
+            ? ((1 << ST_ERR2) | (1 << ST_DX2) | (1 << ST_X2) | (1 << ST_L1) | (1 << ST_NONFIN))
+        : (KIND == COL_ADMM || KIND == COL_ADMM_LAST) ? ((1 << ST_ERR2) | (1 << ST_DX2) | (1 << ST_X2) |
+                                                         (1 << ST_L1) | (1 << ST_R2) | (1 << ST_NONFIN))
+        : 0;
+    if (kSlots) block_stats<kSlots, NT>(acc, kp.pp.partials);
+  }
+  if (E::kFwd) {
+    tile_fft<-1, TILE, NT, TWS>(sm, lay, tw, lgN2);
+#pragma unroll
+    for (int i = 0; i < NLD; ++i) {
+      const int e = 2 * (threadIdx.x + i * NT);
+      if (e < tot) {
+        const int j2 = e >> lgG, c = e & (G - 1);
+        const float2 lo = sm[pad(e)], hi = sm[pad(e + 1)];
+        __stcg(reinterpret_cast<float4*>(W + col0 + c + ((size_t)j2 << g.lgN1)),
+               make_float4(lo.x, lo.y, hi.x, hi.y));
+      }
+    }
+  }
+}
+
+}  // namespace
+
+#define CS_COL_KINDS(X, S)                                                                     \
+  X(COL_LOAD, S) X(COL_LOAD_SCALED, S) X(COL_STORE, S) X(COL_MASK, S) X(COL_RESIDUAL, S)         \
+  X(COL_ISTA, S) X(COL_ISTA_LAST, S) X(COL_POWER_OUT, S) X(COL_ADMM_INIT, S) X(COL_ADMM, S)       \
+  X(COL_ADMM_LAST, S)
+
+cudaError_t init_col_kernels() {
+  cudaError_t e = cudaSuccess;
+#define CS_SET_COL(k, S) if (e == cudaSuccess) e = set_smem(col_kernel<k, S>, COL_TILE, COL_MINB);
+  CS_COL_KINDS(CS_SET_COL, 0)
+  CS_COL_KINDS(CS_SET_COL, 1)
+#undef CS_SET_COL
+  return e;
+}
+
+cudaError_t launch_col(ColKind kind, const KParams& kp, cudaStream_t s) {
+  const Geo& g = kp.geo;
+  const int grid = g.col_ctas;
+  const bool hot = g.lgN2 == 10 && g.lgG == 2;
+#define CS_L_COL(k, S) case k: return launch_k(col_kernel<k, S>, grid, COL_TILE, kp, s);
+  if (hot) {
+    switch (kind) { CS_COL_KINDS(CS_L_COL, 1) }
+  } else {
+    switch (kind) { CS_COL_KINDS(CS_L_COL, 0) }
+  }
+#undef CS_L_COL
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace csk

@@ -1,11 +1,12 @@
 // Shared-memory Stockham FFT building blocks (fp32, sm_103a).
 //
-// A CTA holds up to TILE complex values in shared memory, arranged as `nvec`
+// A CTA holds TILE complex values in shared memory, arranged as `nvec`
 // vectors of length L (a power of two).  One Stockham stage of radix R reads
 // R values per butterfly at stride L/R, twiddles them, applies an in-register
 // DFT_R and writes them back in auto-sorted order, so no bit reversal is ever
 // needed.  Stages use radix 16 while log2(L) allows it and one radix-2/4/8
-// stage for the remainder.
+// stage for the remainder.  Every thread owns EPT = 16 values per stage
+// (TILE = 16 * NT), which keeps a stage within 64 registers.
 //
 // Shared-memory index of linear element e is e + (e >> 4): one pad slot per
 // 16 complex values keeps the stride-16 writes of the first stage free of
@@ -17,9 +18,7 @@
 
 namespace csk {
 
-constexpr int NT = 256;          // threads per CTA of the FFT passes
-constexpr int TILE = 8192;       // complex values per CTA
-constexpr int EPT = TILE / NT;   // complex values per thread
+constexpr int EPT = 16;   // complex values per thread per stage
 
 __host__ __device__ constexpr int smem_slots(int tile) { return tile + (tile >> 4); }
 
@@ -54,105 +53,137 @@ __device__ __forceinline__ float cos16(int j) {
 }
 __device__ __forceinline__ float sin16(int j) { return cos16(j - 4); }
 
-// exp(DIR * 2 pi i j / 16), folded to constants when j is known at compile time
+// a * exp(DIR * 2 pi i j / 16); j is a compile-time constant after unrolling
 template <int DIR>
-__device__ __forceinline__ float2 w16(int j) { return make_float2(cos16(j), DIR * sin16(j)); }
-
-// In-register DFT of length R (R in {2,4,8,16}), natural order in and out:
-// X_k = sum_r a_r exp(DIR 2 pi i r k / R).
-template <int R, int DIR> struct Dft;
-
-template <int DIR> struct Dft<2, DIR> {
-  __device__ __forceinline__ static void run(float2* a) {
-    float2 t = a[1];
-    a[1] = csub(a[0], t);
-    a[0] = cadd(a[0], t);
-  }
-};
-
-template <int DIR> struct Dft<4, DIR> {
-  __device__ __forceinline__ static void run(float2* a) {
-    float2 s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
-    float2 s13 = cadd(a[1], a[3]), d13 = mul_diri<DIR>(csub(a[1], a[3]));
-    a[0] = cadd(s02, s13);
-    a[2] = csub(s02, s13);
-    a[1] = cadd(d02, d13);
-    a[3] = csub(d02, d13);
-  }
-};
-
-// R = P*Q: n = Q*n1 + n2, k = k1 + P*k2.
-//   b[n2][k1] = DFT_P over n1 of a[Q n1 + n2], times w_R^(n2 k1)
-//   X[k1 + P k2] = DFT_Q over n2 of b[n2][k1]
-template <int P, int Q, int DIR>
-__device__ __forceinline__ void dft_split(float2* a) {
-  constexpr int R = P * Q;
-  float2 b[Q][P];
-#pragma unroll
-  for (int n2 = 0; n2 < Q; ++n2) {
-    float2 t[P];
-#pragma unroll
-    for (int n1 = 0; n1 < P; ++n1) t[n1] = a[Q * n1 + n2];
-    Dft<P, DIR>::run(t);
-#pragma unroll
-    for (int k1 = 0; k1 < P; ++k1) {
-      const int j = (n2 * k1 * (16 / R)) & 15;
-      b[n2][k1] = (j == 0) ? t[k1] : cmul(t[k1], w16<DIR>(j));
-    }
-  }
-#pragma unroll
-  for (int k1 = 0; k1 < P; ++k1) {
-    float2 t[Q];
-#pragma unroll
-    for (int n2 = 0; n2 < Q; ++n2) t[n2] = b[n2][k1];
-    Dft<Q, DIR>::run(t);
-#pragma unroll
-    for (int k2 = 0; k2 < Q; ++k2) a[k1 + P * k2] = t[k2];
-  }
+__device__ __forceinline__ float2 rot16(float2 a, int j) {
+  j &= 15;
+  if (j == 0) return a;
+  if (j == 4) return mul_diri<DIR>(a);
+  if (j == 8) return make_float2(-a.x, -a.y);
+  if (j == 12) return mul_diri<-DIR>(a);
+  return cmul(a, make_float2(cos16(j), DIR * sin16(j)));
 }
 
-template <int DIR> struct Dft<8, DIR> {
-  __device__ __forceinline__ static void run(float2* a) { dft_split<4, 2, DIR>(a); }
-};
-template <int DIR> struct Dft<16, DIR> {
-  __device__ __forceinline__ static void run(float2* a) { dft_split<4, 4, DIR>(a); }
-};
+// In-register DFT of length R in {2,4,8,16}: X_k = sum_r a_r exp(DIR 2 pi i r k / R).
+// Computed in place; X_k ends in register slot out_slot<R>(k).
+template <int R> __device__ __forceinline__ constexpr int out_slot(int k) {
+  // R = 4 * Q (Q = R/4) for R >= 8: X[k1 + 4 k2] lands in a[Q k1 + k2]
+  return R <= 4 ? k : (R / 4) * (k % 4) + k / 4;
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  const float2 s13 = cadd(a1, a3), d13 = mul_diri<DIR>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void dft(float2* a) {
+  if (R == 2) {
+    const float2 t = a[1];
+    a[1] = csub(a[0], t);
+    a[0] = cadd(a[0], t);
+  } else if (R == 4) {
+    dft4<DIR>(a[0], a[1], a[2], a[3]);
+  } else {
+    // R = 4 * Q: n = Q n1 + n2, k = k1 + 4 k2
+    constexpr int Q = R / 4;
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) dft4<DIR>(a[n2], a[Q + n2], a[2 * Q + n2], a[3 * Q + n2]);
+    // now a[Q k1 + n2] holds the length-4 transform; twiddle by w_R^(n2 k1)
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1)
+#pragma unroll
+      for (int n2 = 1; n2 < Q; ++n2) a[Q * k1 + n2] = rot16<DIR>(a[Q * k1 + n2], n2 * k1 * (16 / R));
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      if (Q == 2) {
+        const float2 t = a[Q * k1 + 1];
+        a[Q * k1 + 1] = csub(a[Q * k1], t);
+        a[Q * k1] = cadd(a[Q * k1], t);
+      } else {
+        dft4<DIR>(a[Q * k1], a[Q * k1 + 1], a[Q * k1 + 2], a[Q * k1 + 3]);
+      }
+    }
+  }
+}
 
 // Geometry of the vectors held in shared memory.
 //   rows layout (vec_fast = false): element (vec, idx) at vec*L + idx
 //   cols layout (vec_fast = true):  element (vec, idx) at idx*nvec + vec
-struct VecLayout {
+// DynLayout carries the shape at run time; StaticLayout fixes it at compile
+// time for the hot sizes, so every shared-memory address of a stage folds to
+// a base register plus an immediate offset.
+struct DynLayout {
+  static constexpr bool kStatic = false;
   int lgL;      // log2 vector length
   int lgnv;     // log2 number of vectors
   bool vec_fast;
+  __device__ __forceinline__ int LG() const { return lgL; }
+  __device__ __forceinline__ int NV() const { return lgnv; }
+  __device__ __forceinline__ bool VF() const { return vec_fast; }
   __device__ __forceinline__ int at(int vec, int idx) const {
     return vec_fast ? ((idx << lgnv) + vec) : ((vec << lgL) + idx);
   }
 };
 
+template <int LGL, int LGNV, bool VEC_FAST>
+struct StaticLayout {
+  static constexpr bool kStatic = true;
+  static constexpr int kLgL = LGL, kLgNv = LGNV;
+  __device__ __forceinline__ constexpr int LG() const { return LGL; }
+  __device__ __forceinline__ constexpr int NV() const { return LGNV; }
+  __device__ __forceinline__ constexpr bool VF() const { return VEC_FAST; }
+  __device__ __forceinline__ int at(int vec, int idx) const {
+    return VEC_FAST ? ((idx << LGNV) + vec) : ((vec << LGL) + idx);
+  }
+};
+
+// Element hooks: `pre` runs on the values a first stage loads (before its
+// DFT), `post` on the values a last stage produces (before they are stored).
+// In both cases the element's index within its vector (natural order) is
+// j + r * (L / R): butterfly j, slot r.
+struct NoHook {
+  static constexpr bool kPre = false, kPost = false;
+  __device__ __forceinline__ void begin(int, int) {}
+  __device__ __forceinline__ float2 pre(int, int, int, int, float2 v) const { return v; }
+  __device__ __forceinline__ float2 post(int, int, int, int, float2 v) { return v; }
+};
+
 // One Stockham stage of radix R over all vectors of the tile.
 //   Ls   product of the radices of the stages already done
-//   tw   twiddle table tw[q] = exp(-2 pi i q / Lt), Lt = 1 << lgLt >= L
-template <int R, int DIR>
-__device__ __forceinline__ void stockham_stage(float2* s, const VecLayout& lay, int lgLs,
-                                               const float2* __restrict__ tw, int lgLt) {
+//   tw   without TWS: table tw[q] = exp(-2 pi i q / Lt), Lt = 1 << lgLt >= L,
+//        in global memory (read-only path).  With TWS: this stage's block of
+//        the stage-major table in shared memory, tw[(r-1) Ls + k] =
+//        w_{Ls R}^(r k), so the R-1 reads of a butterfly use immediate offsets
+//        and neighbouring threads read neighbouring words.
+template <int R, int DIR, int TILE, int NT, bool TWS, class LAY, class H>
+__device__ __forceinline__ void stockham_stage(float2* s, const LAY& lay, int lgLs,
+                                               const float2* __restrict__ tw, int lgLt, H& hook) {
   constexpr int BPT = TILE / (R * NT);   // butterflies per thread
-  const int lgL = lay.lgL;
-  const int lgLR = lgL - (R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4);  // log2(L/R)
-  const int nb = 1 << (lay.lgnv + lgLR);                                // butterflies in the tile
+  constexpr int lgR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+  const int lgL = lay.LG();
+  const int lgnv = lay.NV();
+  const int lgLR = lgL - lgR;                    // log2(L/R)
+  const int nb = 1 << (lgnv + lgLR);             // butterflies in the tile
   const int Ls = 1 << lgLs;
-  // twiddle index step for w_{Ls R}^(r k): (Lt / (Ls R)) * r * k
-  const int lgstep = lgLt - lgLs - (lgL - lgLR);
+  const int lgstep = lgLt - lgLs - lgR;          // w_{Ls R}^(r k) = tw[(r k) << lgstep]
+  const bool first = lgLs == 0;
+  const bool last = lgLs + lgR == lgL;
   float2 v[BPT][R];
+  int vecs[BPT], js[BPT];
 #pragma unroll
   for (int i = 0; i < BPT; ++i) {
     const int b = threadIdx.x + i * NT;
+    if (lay.VF()) { vecs[i] = b & ((1 << lgnv) - 1); js[i] = b >> lgnv; }
+    else { vecs[i] = b >> lgLR; js[i] = b & ((1 << lgLR) - 1); }
     if (b < nb) {
-      int vec, j;
-      if (lay.vec_fast) { vec = b & ((1 << lay.lgnv) - 1); j = b >> lay.lgnv; }
-      else { vec = b >> lgLR; j = b & ((1 << lgLR) - 1); }
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = s[pad(lay.at(vec, j + (r << lgLR)))];
+      for (int r = 0; r < R; ++r) v[i][r] = s[pad(lay.at(vecs[i], js[i] + (r << lgLR)))];
     }
   }
   __syncthreads();
@@ -160,22 +191,31 @@ __device__ __forceinline__ void stockham_stage(float2* s, const VecLayout& lay, 
   for (int i = 0; i < BPT; ++i) {
     const int b = threadIdx.x + i * NT;
     if (b < nb) {
-      int vec, j;
-      if (lay.vec_fast) { vec = b & ((1 << lay.lgnv) - 1); j = b >> lay.lgnv; }
-      else { vec = b >> lgLR; j = b & ((1 << lgLR) - 1); }
+      const int j = js[i];
       const int k = j & (Ls - 1);
-      if (lgLs > 0) {
+      if (H::kPre && first) {
+        hook.begin(vecs[i], j);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i][r] = hook.pre(vecs[i], j, r, lgLR, v[i][r]);
+      }
+      if (!first) {
+        const int kk = k << lgstep;   // w_{Ls R}^(r k) = tw[r * kk]
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          float2 w = __ldg(tw + ((r * k) << lgstep));
+          float2 w = TWS ? tw[(r - 1) * Ls + k] : __ldg(tw + r * kk);
           if (DIR > 0) w.y = -w.y;
           v[i][r] = cmul(v[i][r], w);
         }
       }
-      Dft<R, DIR>::run(v[i]);
-      const int base = ((j - k) * R) + k;
+      dft<R, DIR>(v[i]);
+      const int base = ((j - k) << lgR) + k;   // in the last stage base == j, Ls == L/R
+      if (H::kPost && last && !(H::kPre && first)) hook.begin(vecs[i], j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) s[pad(lay.at(vec, base + r * Ls))] = v[i][r];
+      for (int r = 0; r < R; ++r) {
+        float2 o = v[i][out_slot<R>(r)];
+        if (H::kPost && last) o = hook.post(vecs[i], j, r, lgLR, o);
+        s[pad(lay.at(vecs[i], base + r * Ls))] = o;
+      }
     }
   }
   __syncthreads();
@@ -184,16 +224,60 @@ __device__ __forceinline__ void stockham_stage(float2* s, const VecLayout& lay, 
 // Full FFT of every vector in the tile (in place, natural order in and out).
 // Forward (DIR = -1): X_k = sum_j x_j exp(-2 pi i jk/L); inverse (DIR = +1)
 // uses exp(+2 pi i jk/L) without the 1/L factor.
-template <int DIR>
-__device__ __forceinline__ void tile_fft(float2* s, const VecLayout& lay, const float2* __restrict__ tw,
-                                         int lgLt) {
-  int lgLs = 0;
-  const int lgL = lay.lgL;
-  while (lgL - lgLs >= 4) { stockham_stage<16, DIR>(s, lay, lgLs, tw, lgLt); lgLs += 4; }
-  const int rem = lgL - lgLs;
-  if (rem == 3) stockham_stage<8, DIR>(s, lay, lgLs, tw, lgLt);
-  else if (rem == 2) stockham_stage<4, DIR>(s, lay, lgLs, tw, lgLt);
-  else if (rem == 1) stockham_stage<2, DIR>(s, lay, lgLs, tw, lgLt);
+template <int DIR, int TILE, int NT, bool TWS = false, class LAY, class H>
+__device__ __forceinline__ void tile_fft(float2* s, const LAY& lay, const float2* __restrict__ tw, int lgLt,
+                                         H& hook) {
+  if constexpr (LAY::kStatic) {
+    constexpr int LGL = LAY::kLgL;
+    // with TWS, stage st (span 16^st) reads block st-1 of the stage-major table
+    int off = 0;
+#pragma unroll
+    for (int st = 0; st < LGL / 4; ++st) {
+      stockham_stage<16, DIR, TILE, NT, TWS>(s, lay, 4 * st, TWS ? tw + off : tw, lgLt, hook);
+      if (st > 0) off += 15 << (4 * st);
+    }
+    constexpr int rem = LGL % 4;
+    const float2* twr = TWS ? tw + off : tw;
+    if constexpr (rem == 3) stockham_stage<8, DIR, TILE, NT, TWS>(s, lay, LGL - 3, twr, lgLt, hook);
+    if constexpr (rem == 2) stockham_stage<4, DIR, TILE, NT, TWS>(s, lay, LGL - 2, twr, lgLt, hook);
+    if constexpr (rem == 1) stockham_stage<2, DIR, TILE, NT, TWS>(s, lay, LGL - 1, twr, lgLt, hook);
+  } else {
+    int lgLs = 0;
+    const int lgL = lay.LG();
+    while (lgL - lgLs >= 4) { stockham_stage<16, DIR, TILE, NT, TWS>(s, lay, lgLs, tw, lgLt, hook); lgLs += 4; }
+    const int rem = lgL - lgLs;
+    if (rem == 3) stockham_stage<8, DIR, TILE, NT, TWS>(s, lay, lgLs, tw, lgLt, hook);
+    else if (rem == 2) stockham_stage<4, DIR, TILE, NT, TWS>(s, lay, lgLs, tw, lgLt, hook);
+    else if (rem == 1) stockham_stage<2, DIR, TILE, NT, TWS>(s, lay, lgLs, tw, lgLt, hook);
+  }
+}
+
+template <int DIR, int TILE, int NT, bool TWS = false, class LAY>
+__device__ __forceinline__ void tile_fft(float2* s, const LAY& lay, const float2* __restrict__ tw, int lgLt) {
+  NoHook h;
+  tile_fft<DIR, TILE, NT, TWS>(s, lay, tw, lgLt, h);
+}
+
+// Entries of the stage-major twiddle table of a length-L FFT: stage s >= 1
+// (span Ls, radix R) contributes (R - 1) * Ls entries.
+__host__ __device__ constexpr int stage_tw_count(int lgL) {
+  int n = 0, lgLs = 0;
+  while (lgLs < lgL) {
+    const int lgR = (lgL - lgLs) >= 4 ? 4 : (lgL - lgLs);
+    if (lgLs > 0) n += ((1 << lgR) - 1) << lgLs;
+    lgLs += lgR;
+  }
+  return n;
+}
+
+// Copy `count` (a multiple of 2) table entries from global to shared memory.
+template <int NT>
+__device__ __forceinline__ void copy_table(float2* dst, const float2* __restrict__ src, int count) {
+  for (int i = 2 * threadIdx.x; i < count; i += 2 * NT) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(src + i));
+    dst[i] = make_float2(v.x, v.y);
+    dst[i + 1] = make_float2(v.z, v.w);
+  }
 }
 
 }  // namespace csk

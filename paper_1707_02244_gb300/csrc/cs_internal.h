@@ -17,10 +17,14 @@ struct Geo {
   int N, lgN, N1, lgN1, N2, lgN2;
   int G, lgG, col_ctas;
   int U, lgU, mid_ctas;
+  int tile;            // mid pass: complex values per CTA (4096 or 8192); threads = tile / 16
   const float2* tw1;   // exp(-2 pi i q / (2 N1)), q < 2 N1
   const float2* tw2;   // exp(-2 pi i q / N2),     q < N2
   const float2* twl;   // exp(-2 pi i q / N),      q < N1
   const float2* twr;   // exp(-2 pi i q / (2 N)),  q < N2
+  const float2* tw1h;  // exp(-2 pi i q / N1),     q < N1
+  const float2* tws1;  // stage-major twiddles of the length-N1 FFT
+  const float2* tws2;  // stage-major twiddles of the length-N2 FFT
 };
 
 constexpr int NSTAT = 8;
@@ -43,7 +47,8 @@ struct PlanPtrs {
   const float* ys;           // y in ascending-row order, [m]
   double* partials;          // [max_ctas * NSTAT]
   double* stats;             // [NSTAT] finalised sums
-  const float4* tab_ista;    // (P, Q) per pair slot, real-FFT geometry
+  const float4* tab_ista;    // (a, a') per pair slot, real-FFT geometry
+  const float2* tab_ista_b;  // b per pair slot
   const float2* tab_admm_c;  // chat_k per pair slot, complex-n geometry
   const float* tab_admm_b;   // 1 / (n (rho |chat_k|^2 + sigma)) per pair slot
   int* status;               // device status word
@@ -95,8 +100,10 @@ enum MidKind : int { MID_FWD = 0, MID_ADJ, MID_ADMM };
 // Launchers (cs_passes.cu).  Return cudaGetLastError() of the launch.
 cudaError_t launch_col(ColKind kind, const KParams& kp, cudaStream_t s);
 cudaError_t launch_mid(MidKind kind, const KParams& kp, cudaStream_t s);
-size_t pass_smem_bytes();
+size_t pass_smem_bytes(int tile);
 cudaError_t init_pass_kernels();
+cudaError_t init_col_kernels();
+cudaError_t init_mid_kernels();
 
 // Small kernels (cs_aux.cu).
 cudaError_t launch_set_args(const CallArgs& a, CallArgs* dst, cudaStream_t s);
@@ -104,8 +111,9 @@ cudaError_t launch_finalize(const double* partials, int nblk, double* stats, cud
 cudaError_t launch_twiddle(float2* dst, int count, int64_t M, cudaStream_t s);
 cudaError_t launch_fft64(const double* c, double2* a, double2* b, int64_t n, double2** out,
                          cudaStream_t s);
-cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tab,
+cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tabA, float2* tabB,
                             cudaStream_t s);
+cudaError_t launch_stage_tw(float2* dst, int lgL, int count, cudaStream_t s);
 cudaError_t launch_tab_admm(const double2* chat, const Geo& g, int64_t n, float2* tabc,
                             double* abs2, cudaStream_t s);
 cudaError_t launch_tab_admm_b(const double* abs2, int count, int64_t n, double rho,

@@ -1,0 +1,307 @@
+// Mid pass of the fused FFT iteration: forward length-N1 FFTs along the rows
+// of the N2 x N1 exchange array (with the four-step twiddle), the spectrum
+// operator over every (k, N - k) pair, and the inverse FFTs.
+#include "cs_passes.cuh"
+
+namespace csk {
+
+namespace {
+
+// ---------------------------------------------------------------- mid pass
+
+// w_N^(j1 k2) from the two-level table: w_N^p = w_N^(p mod N1) * w_N2^(p div N1)
+__device__ __forceinline__ float2 tw4(const Geo& g, int p) {
+  return cmul(__ldg(g.twl + (p & (g.N1 - 1))), __ldg(g.tw2 + (p >> g.lgN1)));
+}
+
+__device__ __forceinline__ int slot_row(const Geo& g, int u, int second) {
+  if (u == 0) return second ? (g.N2 >> 1) : 0;
+  return second ? g.N2 - u : u;
+}
+
+// Four-step twiddle as FFT hooks: w_N^(j1 k2) on the values the first
+// forward stage loads, its conjugate on the values the last inverse stage
+// produces (k2 = the tile row's index in the N2 x N1 array).  With
+// j1 = j + r L/R:  w_N^(j1 k2) = w_N^(j k2) * w_N^(r (L/R) k2); the second
+// factor comes from a per-CTA table rt[row][r] in shared memory.
+constexpr int MID_MAX_ROWS = 64;   // 2U <= min(N2, TILE/N1) <= 64 rows, as N2 <= N1
+
+// Static shapes: w_N^(j1 k2) = lo[j1 mod 16] * hi[j1 div 16], two per-row
+// tables of 16 and N1/16 entries (both exact FP64-rounded values).  With
+// j1 = j + r L/R and L/R >= 16, lo depends on the thread only and hi is read
+// at (j div 16) + r (L/R)/16.
+template <bool PRE>
+struct MidTwHookS {
+  static constexpr bool kPre = PRE, kPost = !PRE;
+  const float2* lo;   // [rows][16]
+  const float2* hi;   // [rows][N1/16]
+  int lgN1;
+  float2 wl;
+  __device__ __forceinline__ void begin(int vec, int j) { wl = lo[vec * 16 + (j & 15)]; }
+  __device__ __forceinline__ float2 tw(int vec, int j, int r, int lgLR) const {
+    return cmul(wl, hi[(vec << (lgN1 - 4)) + (j >> 4) + (r << (lgLR - 4))]);
+  }
+  __device__ __forceinline__ float2 pre(int vec, int j, int r, int lgLR, float2 v) const {
+    return cmul(v, tw(vec, j, r, lgLR));
+  }
+  __device__ __forceinline__ float2 post(int vec, int j, int r, int lgLR, float2 v) {
+    return cmulc(v, tw(vec, j, r, lgLR));
+  }
+};
+
+template <bool PRE>
+struct MidTwHook {
+  static constexpr bool kPre = PRE, kPost = !PRE;
+  const Geo& g;
+  int u0;
+  const float2* rt;   // [2U][16]
+  float2 wj;
+  __device__ __forceinline__ void begin(int vec, int j) {
+    wj = tw4(g, j * slot_row(g, u0 + (vec >> 1), vec & 1));
+  }
+  __device__ __forceinline__ float2 pre(int vec, int, int r, int, float2 v) const {
+    return cmul(v, cmul(wj, rt[vec * 16 + r]));
+  }
+  __device__ __forceinline__ float2 post(int vec, int, int r, int, float2 v) {
+    return cmulc(v, cmul(wj, rt[vec * 16 + r]));
+  }
+};
+// Real-FFT spectrum operator (products with C and C^T on the packed vector).
+// For the pair (k, N - k) of the packed spectrum Z, with H the real-signal
+// spectrum of the product (H = chat for C^T, conj(chat) for C):
+//   Z'_k   = a  Z_k   + b  conj(Z_{N-k})
+//   Z'_N-k = a' Z_N-k + b' conj(Z_k),   b' = -conj(b)
+// where (a, a', b) are tabulated for H = chat (FP64 at plan time: a = P - Q sin,
+// a' = conj(P + Q sin), b = i Q cos, P = (H_k + H_{k+N})/2N, Q = (H_k - H_{k+N})/2N,
+// angle 2 pi k / 2N).  H = conj(chat) conjugates a and a' and maps b -> -conj(b).
+template <bool ADJ>
+__device__ __forceinline__ void op_real(const PlanPtrs& pp, int tidx, float2& za, float2& zb) {
+  const float4 t = __ldg(pp.tab_ista + tidx);
+  float2 al = make_float2(t.x, t.y), al2 = make_float2(t.z, t.w);
+  float2 be = __ldg(pp.tab_ista_b + tidx);
+  float2 be2 = make_float2(-be.x, be.y);
+  if (!ADJ) {
+    al = cconj(al);
+    al2 = cconj(al2);
+    const float2 tb = be;
+    be = make_float2(-tb.x, tb.y);
+    be2 = tb;
+  }
+  const float2 a2 = za, b2 = zb;
+  za = cadd(cmul(al, a2), cmul(be, cconj(b2)));
+  zb = cadd(cmul(al2, b2), cmul(be2, cconj(a2)));
+}
+
+// Complex-n ADMM operator for the pair (k, N - k) of Z = FFT((v) + i (z - nu)):
+//   V = (Z_k + conj Z_{N-k}) / 2,  Wk = (Z_k - conj Z_{N-k}) / 2i
+//   X = bhat (rho chat V + sigma Wk) / N            (x-update, Algorithm 3)
+//   Pc = conj(chat) X                                 (spectrum of C x)
+//   Z'_k = X + i Pc,  Z'_{N-k} = conj(X) + i conj(Pc)
+__device__ __forceinline__ void op_admm(const PlanPtrs& pp, const CallArgs& a, int tidx,
+                                        float2& za, float2& zb) {
+  const float2 ch = __ldg(pp.tab_admm_c + tidx);
+  const float bb = __ldg(pp.tab_admm_b + tidx);
+  const float2 V = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+  const float2 Wk = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+  const float2 cv = cmul(ch, V);
+  const float2 X = make_float2(bb * fmaf(a.rho, cv.x, a.sigma * Wk.x),
+                               bb * fmaf(a.rho, cv.y, a.sigma * Wk.y));
+  const float2 Pc = cmulc(X, ch);
+  za = make_float2(X.x - Pc.y, X.y + Pc.x);
+  zb = make_float2(X.x + Pc.y, Pc.x - X.y);
+}
+
+// SHAPE 0: any geometry; SHAPE s > 0 fixes (log2 N1, log2 U) at compile time
+// for the geometries of N = 2^20 (1024 x 1024, U = 2), 2^21 (2048 x 1024,
+// U = 1) and 2^22 (4096 x 1024, U = 1).
+template <int SHAPE> struct MidShape;
+template <> struct MidShape<0> {
+  using Lay = DynLayout;
+  __device__ static Lay lay(const Geo& g) { return Lay{g.lgN1, g.lgU + 1, false}; }
+  __device__ static int lgN1(const Geo& g) { return g.lgN1; }
+  __device__ static int lgU(const Geo& g) { return g.lgU; }
+};
+template <int LGN1, int LGU> struct MidShapeS {
+  using Lay = StaticLayout<LGN1, LGU + 1, false>;
+  __device__ static Lay lay(const Geo&) { return Lay{}; }
+  __device__ static constexpr int lgN1(const Geo&) { return LGN1; }
+  __device__ static constexpr int lgU(const Geo&) { return LGU; }
+};
+template <> struct MidShape<1> : MidShapeS<10, 1> {};
+template <> struct MidShape<2> : MidShapeS<11, 0> {};
+template <> struct MidShape<3> : MidShapeS<12, 0> {};
+
+template <int KIND, int TILE, int SHAPE>
+__global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(const KParams kp) {
+  constexpr int NT = Cfg<TILE>::NT;
+  constexpr int NLD = Cfg<TILE>::NLD;
+  using S = MidShape<SHAPE>;
+  extern __shared__ float2 sm[];
+  const Geo& g = kp.geo;
+  const int lgU = S::lgU(g), U = 1 << lgU;
+  const int u0 = blockIdx.x << lgU;
+  const int lgN1 = S::lgN1(g), N1 = 1 << lgN1;
+  const int tot = (2 * U) << lgN1;
+  const auto lay = S::lay(g);
+  float2* __restrict__ W = kp.pp.W;
+  constexpr bool TWS = SHAPE != 0;   // static shape: twiddles in shared memory
+  constexpr int LGN1S = SHAPE == 0 ? 4 : S::lgN1(Geo{});
+  constexpr int ROWS = SHAPE == 0 ? MID_MAX_ROWS : (2 << S::lgU(Geo{}));
+  constexpr int TW_N = SHAPE == 0 ? 2 : stage_tw_count(LGN1S);
+  __shared__ __align__(16) float2 tws[TW_N];
+  // static shapes: per-row lo[16] and hi[N1/16]; dynamic: rt (see MidTwHook)
+  constexpr int LOHI = SHAPE == 0 ? 2 : ROWS * (16 + (1 << (LGN1S - 4)));
+  __shared__ float2 lohi[LOHI];
+  __shared__ float2 rt[2][SHAPE == 0 ? MID_MAX_ROWS * 16 : 2];
+  if (TWS) {
+    copy_table<NT>(tws, g.tws1, TW_N);
+    constexpr int HI = 1 << (LGN1S - 4);
+    for (int t = threadIdx.x; t < ROWS * (16 + HI); t += NT) {
+      const bool is_lo = t < ROWS * 16;
+      const int tt = is_lo ? t : t - ROWS * 16;
+      const int vec = is_lo ? (tt >> 4) : (tt >> (LGN1S - 4));
+      const int q = is_lo ? (tt & 15) : (tt & (HI - 1)) << 4;
+      const int k2 = slot_row(g, u0 + (vec >> 1), vec & 1);
+      lohi[t] = tw4(g, (q * k2) & (g.N - 1));
+    }
+  } else {
+    // rt[0][row][r] = w_N^(r (L/R) k2) for R the radix of the first stage (the
+    // forward pre-hook), rt[1] for the radix of the last stage (inverse post-hook)
+    const int lgRf = lgN1 >= 4 ? 4 : lgN1;
+    const int lgRl = (lgN1 & 3) ? (lgN1 & 3) : 4;
+    for (int t = threadIdx.x; t < 2 * 2 * U * 16; t += NT) {
+      const int which = t / (2 * U * 16);
+      const int tt = t - which * (2 * U * 16);
+      const int vec = tt >> 4, r = tt & 15;
+      const int lgR = which ? lgRl : lgRf;
+      const int k2 = slot_row(g, u0 + (vec >> 1), vec & 1);
+      rt[which][tt] = r < (1 << lgR) ? tw4(g, ((r << (lgN1 - lgR)) * k2) & (g.N - 1)) : make_float2(1.f, 0.f);
+    }
+  }
+  {
+    float4 buf[NLD];
+#pragma unroll
+    for (int i = 0; i < NLD; ++i) {
+      const int e = 2 * (threadIdx.x + i * NT);
+      if (e < tot) {
+        const int slot = e >> lgN1, j1 = e & (N1 - 1);
+        const int k2 = slot_row(g, u0 + (slot >> 1), slot & 1);
+        buf[i] = __ldcg(reinterpret_cast<const float4*>(W + ((size_t)k2 << lgN1) + j1));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NLD; ++i) {
+      const int e = 2 * (threadIdx.x + i * NT);
+      if (e < tot) {
+        sm[pad(e)] = make_float2(buf[i].x, buf[i].y);
+        sm[pad(e + 1)] = make_float2(buf[i].z, buf[i].w);
+      }
+    }
+  }
+  __syncthreads();
+  if constexpr (TWS) {
+    MidTwHookS<true> h{lohi, lohi + ROWS * 16, LGN1S, make_float2(1.f, 0.f)};
+    tile_fft<-1, TILE, NT, true>(sm, lay, tws, lgN1, h);
+  } else {
+    MidTwHook<true> h{g, u0, rt[0], make_float2(1.f, 0.f)};
+    tile_fft<-1, TILE, NT, false>(sm, lay, g.tw1, lgN1 + 1, h);
+  }
+
+  // spectrum operator over all (k, N-k) pairs held by this CTA
+  const CallArgs a = *kp.ca;
+  const int nslots = (U << lgN1) + (u0 == 0 ? 1 : 0);
+  const int base_u1 = ((g.N2 >> 1) - 1) << lgN1;   // table offset of unit 0
+  for (int t = threadIdx.x; t < nslots; t += NT) {
+    int ul, q;
+    if (t < (U << lgN1)) { ul = t >> lgN1; q = t & (N1 - 1); }
+    else { ul = 0; q = N1; }
+    const int u = u0 + ul;
+    int ea, eb, k2, k1, tidx;
+    if (u > 0) {
+      k2 = u; k1 = q;
+      ea = ((2 * ul) << lgN1) + q;
+      eb = ((2 * ul + 1) << lgN1) + (N1 - 1 - q);
+      tidx = ((u - 1) << lgN1) + q;
+    } else if (q <= (N1 >> 1)) {
+      k2 = 0; k1 = q;
+      ea = ((2 * ul) << lgN1) + q;
+      eb = ((2 * ul) << lgN1) + ((N1 - q) & (N1 - 1));
+      tidx = base_u1 + q;
+    } else {
+      const int qq = q - (N1 >> 1) - 1;
+      k2 = g.N2 >> 1; k1 = qq;
+      ea = ((2 * ul + 1) << lgN1) + qq;
+      eb = ((2 * ul + 1) << lgN1) + (N1 - 1 - qq);
+      tidx = base_u1 + q;
+    }
+    float2 za = sm[pad(ea)], zb = sm[pad(eb)];
+    if (KIND == MID_ADMM) op_admm(kp.pp, a, tidx, za, zb);
+    else op_real<KIND == MID_ADJ>(kp.pp, tidx, za, zb);
+    sm[pad(eb)] = zb;   // self-pairs (ea == eb) keep the k-side value
+    sm[pad(ea)] = za;
+  }
+  __syncthreads();
+  if constexpr (TWS) {
+    MidTwHookS<false> h{lohi, lohi + ROWS * 16, LGN1S, make_float2(1.f, 0.f)};
+    tile_fft<+1, TILE, NT, true>(sm, lay, tws, lgN1, h);
+  } else {
+    MidTwHook<false> h{g, u0, rt[1], make_float2(1.f, 0.f)};
+    tile_fft<+1, TILE, NT, false>(sm, lay, g.tw1, lgN1 + 1, h);
+  }
+
+#pragma unroll
+  for (int i = 0; i < NLD; ++i) {
+    const int e = 2 * (threadIdx.x + i * NT);
+    if (e < tot) {
+      const int slot = e >> lgN1, j1 = e & (N1 - 1);
+      const int k2 = slot_row(g, u0 + (slot >> 1), slot & 1);
+      const float2 lo = sm[pad(e)], hi = sm[pad(e + 1)];
+      __stcg(reinterpret_cast<float4*>(W + ((size_t)k2 << lgN1) + j1), make_float4(lo.x, lo.y, hi.x, hi.y));
+    }
+  }
+}
+
+}  // namespace
+
+#define CS_MID_KINDS(X, T, S) X(MID_FWD, T, S) X(MID_ADJ, T, S) X(MID_ADMM, T, S)
+
+cudaError_t init_mid_kernels() {
+  cudaError_t e = cudaSuccess;
+#define CS_SET_MID(k, T, S) if (e == cudaSuccess) e = set_smem(mid_kernel<k, T, S>, T, Cfg<T>::MINB);
+  CS_MID_KINDS(CS_SET_MID, 4096, 0)
+  CS_MID_KINDS(CS_SET_MID, 8192, 0)
+  CS_MID_KINDS(CS_SET_MID, 4096, 1)
+  CS_MID_KINDS(CS_SET_MID, 4096, 2)
+  CS_MID_KINDS(CS_SET_MID, 8192, 3)
+#undef CS_SET_MID
+  return e;
+}
+
+cudaError_t launch_mid(MidKind kind, const KParams& kp, cudaStream_t s) {
+  const Geo& g = kp.geo;
+  const int grid = g.mid_ctas;
+  int shape = 0;
+  if (g.lgN1 == 10 && g.lgU == 1 && g.tile == 4096) shape = 1;
+  if (g.lgN1 == 11 && g.lgU == 0 && g.tile == 4096) shape = 2;
+  if (g.lgN1 == 12 && g.lgU == 0 && g.tile == 8192) shape = 3;
+#define CS_L_MID(k, T, S) case k: return launch_k(mid_kernel<k, T, S>, grid, T, kp, s);
+  switch (shape) {
+    case 1: switch (kind) { CS_MID_KINDS(CS_L_MID, 4096, 1) } break;
+    case 2: switch (kind) { CS_MID_KINDS(CS_L_MID, 4096, 2) } break;
+    case 3: switch (kind) { CS_MID_KINDS(CS_L_MID, 8192, 3) } break;
+    default:
+      if (g.tile == 4096) { switch (kind) { CS_MID_KINDS(CS_L_MID, 4096, 0) } }
+      else { switch (kind) { CS_MID_KINDS(CS_L_MID, 8192, 0) } }
+  }
+#undef CS_L_MID
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t init_pass_kernels() {
+  cudaError_t e = init_col_kernels();
+  return e == cudaSuccess ? init_mid_kernels() : e;
+}
+
+size_t pass_smem_bytes(int tile) { return sizeof(float2) * (size_t)smem_slots(tile); }
+
+}  // namespace csk

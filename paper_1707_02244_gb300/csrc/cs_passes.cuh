@@ -1,0 +1,269 @@
+// Fused FFT passes of the ISTA / ADMM iterations (fp32, sm_103a): shared
+// pieces of the column pass (cs_col.cu) and the mid pass (cs_mid.cu).
+//
+// Every circulant product is a convolution (Sec. 4.2: circulant matrices are
+// diagonalised by the DFT).  A length-N complex FFT is split four-step into an
+// N2 x N1 array: the column pass runs the length-N2 FFTs, the mid pass the
+// length-N1 FFTs plus the inter-pass twiddle.  A convolution is therefore
+//   column pass (forward)  ->  mid pass (forward, spectrum op, inverse)
+//   ->  column pass (inverse)
+// and the elementwise work of the method (residual on the kept rows,
+// soft threshold, the ADMM updates) is fused into the column pass between the
+// inverse FFT of one product and the forward FFT of the next.
+//
+// Real-FFT geometry (ISTA, products with C and C^T): a real n-vector is
+// packed as n/2 complex values (x_2p + i x_2p+1); the mid pass combines the
+// spectra at k and N-k so that the packed spectrum is multiplied by the
+// circulant's real-signal spectrum without ever being unpacked.
+// Complex-n geometry (ADMM): (v + mu) + i (z - nu) is one complex FFT whose
+// k / N-k pairs give both real spectra; the x-update solve with
+// B = (rho C^T C + sigma I)^-1 is a spectrum multiply (Sec. 4.3), and
+// x + i C x comes back from one inverse FFT.
+#pragma once
+
+#include <type_traits>
+
+#include "cs_fft.cuh"
+#include "cs_internal.h"
+
+namespace csk {
+
+namespace {
+
+__device__ __forceinline__ float soft(float u, float g) {
+  // Eq. 4: sgn(u)(|u| - g) for |u| > g, else 0
+  return u > g ? u - g : (u < -g ? u + g : 0.f);
+}
+
+constexpr int NACC = ST_NONFIN + 1;   // accumulated statistic slots
+
+struct Acc {
+  float v[NACC];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NACC; ++i) v[i] = 0.f;
+  }
+};
+
+// Block reduction of the per-thread accumulators into partials[block].
+// Deterministic: fixed shuffle tree, fixed warp order.  SLOTS is a bit mask.
+template <int SLOTS, int NT>
+__device__ void block_stats(const Acc& a, double* partials) {
+  __shared__ double red[NT / 32][NSTAT];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) {
+    if (!((SLOTS >> k) & 1)) continue;
+    double d = (double)a.v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    if (lane == 0) red[wid][k] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x < NSTAT && ((SLOTS >> threadIdx.x) & 1)) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
+    partials[blockIdx.x * NSTAT + threadIdx.x] = s;
+  }
+}
+
+// Row-of-Omega test and compact y index for spatial row i.
+struct RowSel {
+  const uint32_t* __restrict__ mask;
+  const uint32_t* __restrict__ prefix;
+  __device__ __forceinline__ bool get(int i, int& idx) const {
+    const uint32_t w = __ldg(mask + (i >> 5));
+    const int b = i & 31;
+    idx = (int)__ldg(prefix + (i >> 5)) + __popc(w & ((1u << b) - 1u));
+    return (w >> b) & 1u;
+  }
+  // rows 2p and 2p+1 (same mask word): returns the two bits, idx of row 2p
+  __device__ __forceinline__ uint32_t get2(int p, int& idx) const {
+    const uint32_t w = __ldg(mask + (p >> 4));
+    const int b = (2 * p) & 31;
+    idx = (int)__ldg(prefix + (p >> 4)) + __popc(w & ((1u << b) - 1u));
+    return (w >> b) & 3u;
+  }
+};
+
+__device__ __forceinline__ float2 ld2(const float* p, int i) {
+  return __ldg(reinterpret_cast<const float2*>(p) + i);
+}
+
+// ---------------------------------------------------------------- epilogues
+// apply(v, p, acc): v is the inverse-FFT output at complex index p (when the
+// kind reads the exchange buffer); returns the forward-FFT input at p.
+
+template <int KIND> struct Epi;
+
+template <> struct Epi<COL_LOAD> {
+  static constexpr bool kRead = false, kFwd = true;
+  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2, int p, Acc&) {
+    return ld2(a.src, p);
+  }
+};
+
+template <> struct Epi<COL_LOAD_SCALED> {
+  static constexpr bool kRead = false, kFwd = true;
+  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2, int p, Acc&) {
+    const float s = (float)rsqrt(kp.pp.stats[ST_X2]);
+    float2 u = cscale(ld2(a.src, p), s);
+    reinterpret_cast<float2*>(a.aux)[p] = u;
+    return u;
+  }
+};
+
+template <> struct Epi<COL_STORE> {
+  static constexpr bool kRead = true, kFwd = false;
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2 v, int p, Acc&) {
+    reinterpret_cast<float2*>(a.dst)[p] = v;
+    return v;
+  }
+};
+
+template <> struct Epi<COL_MASK> {
+  static constexpr bool kRead = true, kFwd = true;
+  __device__ static float2 apply(const KParams& kp, const CallArgs&, float2 v, int p, Acc&) {
+    RowSel rs{kp.pp.mask, kp.pp.prefix};
+    int i0;
+    const uint32_t mm = rs.get2(p, i0);
+    return make_float2((mm & 1u) ? v.x : 0.f, (mm & 2u) ? v.y : 0.f);
+  }
+};
+
+// r~ = M (P^T y - C x): residual of Algorithm 1 on the kept rows, zero off
+// them, so that the next product gives A^T r = C^T P^T r.
+template <> struct Epi<COL_RESIDUAL> {
+  static constexpr bool kRead = true, kFwd = true;
+  __device__ static float2 apply(const KParams& kp, const CallArgs&, float2 v, int p, Acc& acc) {
+    RowSel rs{kp.pp.mask, kp.pp.prefix};
+    int i0;
+    const uint32_t mm = rs.get2(p, i0);
+    const float r0 = (mm & 1u) ? __ldg(kp.pp.ys + i0) - v.x : 0.f;
+    const float r1 = (mm & 2u) ? __ldg(kp.pp.ys + i0 + (int)(mm & 1u)) - v.y : 0.f;
+    acc.v[ST_R2] = fmaf(r0, r0, fmaf(r1, r1, acc.v[ST_R2]));
+    return make_float2(r0, r1);
+  }
+};
+
+// x(t) = eta_{tau lambda}[x(t-1) + tau A^T r(t)]  (Algorithm 1, Eq. 4)
+template <bool FWD> struct EpiIsta {
+  static constexpr bool kRead = true, kFwd = FWD;
+  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2 g, int p, Acc& acc) {
+    float2* x = reinterpret_cast<float2*>(a.x);
+    const float2 xo = x[p];
+    float2 xn;
+    xn.x = soft(fmaf(a.tau, g.x, xo.x), a.thr);
+    xn.y = soft(fmaf(a.tau, g.y, xo.y), a.thr);
+    x[p] = xn;
+    if (kp.flags & FL_STATS) {
+      const float d0 = xn.x - xo.x, d1 = xn.y - xo.y;
+      acc.v[ST_DX2] = fmaf(d0, d0, fmaf(d1, d1, acc.v[ST_DX2]));
+      acc.v[ST_X2] = fmaf(xn.x, xn.x, fmaf(xn.y, xn.y, acc.v[ST_X2]));
+      acc.v[ST_L1] += fabsf(xo.x) + fabsf(xo.y);
+      if (a.xtrue) {
+        const float2 t = ld2(a.xtrue, p);
+        const float e0 = xn.x - t.x, e1 = xn.y - t.y;
+        acc.v[ST_ERR2] = fmaf(e0, e0, fmaf(e1, e1, acc.v[ST_ERR2]));
+      }
+      if (!isfinite(xn.x) || !isfinite(xn.y)) acc.v[ST_NONFIN] += 1.f;
+    }
+    return xn;
+  }
+};
+template <> struct Epi<COL_ISTA> : EpiIsta<true> {};
+template <> struct Epi<COL_ISTA_LAST> : EpiIsta<false> {};
+
+template <> struct Epi<COL_POWER_OUT> {
+  static constexpr bool kRead = true, kFwd = false;
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2 w, int p, Acc& acc) {
+    const float2 u = ld2(a.aux, p);
+    reinterpret_cast<float2*>(a.dst)[p] = w;
+    acc.v[ST_X2] = fmaf(w.x, w.x, fmaf(w.y, w.y, acc.v[ST_X2]));
+    acc.v[ST_DX2] = fmaf(u.x, w.x, fmaf(u.y, w.y, acc.v[ST_DX2]));
+    return w;
+  }
+};
+
+// Complex-n geometry: p is the spatial index itself.
+template <> struct Epi<COL_ADMM_INIT> {
+  static constexpr bool kRead = false, kFwd = true;
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2, int p, Acc&) {
+    return make_float2(a.v[p], a.z[p] - a.nu[p]);
+  }
+};
+
+// Algorithm 3, after the x-update: v = D(rho C x - rho mu + P^T y),
+// z = eta_{lambda/sigma}(x + nu), mu += tau1 (v - C x), nu += tau2 (x - z),
+// v <- v + mu; the next x-update reads (v) + i (z - nu).
+template <bool FWD> struct EpiAdmm {
+  static constexpr bool kRead = true, kFwd = FWD;
+  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2 xc, int p, Acc& acc) {
+    RowSel rs{kp.pp.mask, kp.pp.prefix};
+    int iy;
+    const bool on = rs.get(p, iy);
+    const float yv = on ? __ldg(kp.pp.ys + iy) : 0.f;
+    const float x = xc.x, cx = xc.y;
+    const float mu = a.mu[p], nu = a.nu[p];
+    const float d = on ? a.d_on : a.d_off;
+    const float v = d * fmaf(a.rho, cx - mu, yv);
+    const float z = soft(x + nu, a.thr);
+    const float mu2 = fmaf(a.tau1, v - cx, mu);
+    const float nu2 = fmaf(a.tau2, x - z, nu);
+    const float vf = v + mu2;
+    a.mu[p] = mu2;
+    a.nu[p] = nu2;
+    if (kp.flags & FL_WRITE_STATE) {
+      a.z[p] = z;
+      a.v[p] = vf;
+      if (a.x) a.x[p] = x;
+    }
+    if (kp.flags & FL_STATS) {
+      if (a.xtrue) {
+        const float e = z - __ldg(a.xtrue + p);
+        acc.v[ST_ERR2] = fmaf(e, e, acc.v[ST_ERR2]);
+      }
+      const float pr = x - z;
+      acc.v[ST_DX2] = fmaf(pr, pr, acc.v[ST_DX2]);
+      acc.v[ST_X2] = fmaf(z, z, acc.v[ST_X2]);
+      acc.v[ST_L1] += fabsf(z);
+      const float r = on ? yv - cx : 0.f;
+      acc.v[ST_R2] = fmaf(r, r, acc.v[ST_R2]);
+      if (!isfinite(z) || !isfinite(vf)) acc.v[ST_NONFIN] += 1.f;
+    }
+    return make_float2(vf, z - nu2);
+  }
+};
+template <> struct Epi<COL_ADMM> : EpiAdmm<true> {};
+template <> struct Epi<COL_ADMM_LAST> : EpiAdmm<false> {};
+
+template <int TILE> struct Cfg {
+  static constexpr int NT = TILE / EPT;                 // threads per CTA
+  static constexpr int MINB = 65536 / (64 * NT);        // mid pass: CTAs per SM at <= 64 registers
+  static constexpr int NLD = TILE / (2 * NT);           // float4 loads per thread per tile
+};
+
+template <typename K>
+cudaError_t launch_k(K kern, int grid, int tile, const KParams& kp, cudaStream_t s) {
+  kern<<<grid, tile / EPT, pass_smem_bytes(tile), s>>>(kp);
+  return cudaGetLastError();
+}
+
+// Opt a kernel into its dynamic shared memory and ask for a carveout just
+// large enough for `ctas` resident CTAs, leaving the rest of the unified
+// L1 / shared array to L1 (where the twiddle tables live).
+template <typename K>
+cudaError_t set_smem(K kern, int tile, int ctas) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem_bytes(tile));
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  const size_t per_cta = pass_smem_bytes(tile) + fa.sharedSizeBytes + 1024;
+  int pct = (int)((per_cta * ctas * 100 + 228 * 1024 - 1) / (228 * 1024));
+  if (pct > 100) pct = 100;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
+}  // namespace
+}  // namespace csk

@@ -155,6 +155,31 @@ cs_status cs_admm_ex(cs_plan_t plan, const float* y, float lambda,
  * (pass_id, reps < 1, no earlier solve of that kind). */
 cs_status cs_profile_pass(cs_plan_t plan, int pass_id, int reps);
 
+/* Largest n accepted by cs_circulant_apply_static. */
+#define CS_STATIC_MAX_N 16384
+
+/* Allocation-free circulant product (no counterpart in the paper).
+ * For callers that cannot call cudaMalloc: code whose device memory is all
+ * owned by another allocator (a framework's caching allocator or a fixed
+ * pool), and latency-critical loops that cannot take the device
+ * synchronisation an allocation may cause.  No plan is needed and nothing
+ * is allocated: the FFT work space is a fixed 768 KiB array inside this
+ * library, held on every GPU that loads it until the process exits.
+ *   y = C x (transpose = 0) or C^T x (transpose != 0), C[i][j] = c[(j-i) mod n]
+ *   n          power of two, 64 <= n <= CS_STATIC_MAX_N (else CS_ERR_UNSUPPORTED)
+ *   c          DEVICE float64[n], first row of C
+ *   x, y       DEVICE float32[n]
+ *   stream     cudaStream_t (NULL = legacy default stream)
+ * Computed in FP64 (FFT of c and x, spectrum product, inverse FFT), rounded
+ * to fp32 once.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call uses the same array and
+ * overwrites all of it that it reads, so calls that overlap on the GPU race:
+ * order them on one stream.  Asynchronous; errors: CS_ERR_ARG (null pointer),
+ * CS_ERR_UNSUPPORTED (n), CS_ERR_CUDA. */
+cs_status cs_circulant_apply_static(int64_t n, const double* c, const float* x, float* y,
+                                    int transpose, void* stream);
+
 /* Wait for the plan's stream and return the latched device status
  * (CS_OK, CS_ERR_NONFINITE, CS_ERR_TIMEOUT), then clear it. */
 cs_status cs_status_sync(cs_plan_t plan);

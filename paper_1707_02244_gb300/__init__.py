@@ -24,7 +24,7 @@ CS_OK, CS_ERR_ARG, CS_ERR_NOMEM, CS_ERR_CUDA, CS_ERR_TIMEOUT, CS_ERR_NONFINITE, 
 
 EXPORTS = ("cs_plan", "cs_plan_destroy", "cs_opnorm2", "cs_forward", "cs_adjoint",
            "cs_set_monitor", "cs_ista", "cs_admm", "cs_admm_ex", "cs_status_sync",
-           "cs_status_string", "cs_version", "cs_profile_pass")
+           "cs_status_string", "cs_version", "cs_profile_pass", "cs_circulant_apply_static")
 
 
 class CsStats(ctypes.Structure):
@@ -67,6 +67,7 @@ def _load() -> ctypes.CDLL:
                        ctypes.POINTER(CsStats)],
         "cs_status_sync": [vp],
         "cs_profile_pass": [vp, ci, ci],
+        "cs_circulant_apply_static": [i64, vp, vp, vp, ci, vp],
         "cs_status_string": [ci],
         "cs_version": [],
     }
@@ -200,6 +201,14 @@ def cs_admm_ex(plan: Plan, y, lam: float, sigma: float, rho: float, tau1: float,
 
 def cs_profile_pass(plan: Plan, pass_id: int, reps: int = 1):
     _check(_lib.cs_profile_pass(plan.handle, int(pass_id), int(reps)), "cs_profile_pass")
+
+
+def cs_circulant_apply_static(n: int, c, x, y, transpose: bool = False, stream=None):
+    """y = C x (or C^T x) with no plan and no allocation (n <= 16384);
+    c is a float64 device tensor / address, x and y float32."""
+    cptr = int(c.data_ptr()) if hasattr(c, "data_ptr") else int(c)
+    _check(_lib.cs_circulant_apply_static(int(n), cptr, _ptr(x), _ptr(y), int(bool(transpose)),
+                                          _stream_handle(stream)), "cs_circulant_apply_static")
 
 
 def cs_status_sync(plan: Plan) -> int:

@@ -273,6 +273,17 @@ cudaError_t launch_fft64(const double* c, double2* a, double2* b, int64_t n, dou
   return cudaGetLastError();
 }
 
+cudaError_t launch_fft64_complex(double2* a, double2* b, int64_t n, double2** out, cudaStream_t s) {
+  double2* in = a;
+  double2* o = b;
+  for (int64_t Ls = 1; Ls < n; Ls <<= 1) {
+    fft64_stage_k<<<blocks_for(n >> 1), AUX_NT, 0, s>>>(in, o, n, Ls);
+    double2* t = in; in = o; o = t;
+  }
+  *out = in;
+  return cudaGetLastError();
+}
+
 static int64_t tab_count(const Geo& g) { return ((int64_t)(g.N2 >> 1) << g.lgN1) + 1; }
 
 cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tabA, float2* tabB,

@@ -111,6 +111,9 @@ cudaError_t launch_finalize(const double* partials, int nblk, double* stats, cud
 cudaError_t launch_twiddle(float2* dst, int count, int64_t M, cudaStream_t s);
 cudaError_t launch_fft64(const double* c, double2* a, double2* b, int64_t n, double2** out,
                          cudaStream_t s);
+// Forward FP64 FFT of the complex vector in a (b is work space); *out is
+// whichever of a / b holds the result.
+cudaError_t launch_fft64_complex(double2* a, double2* b, int64_t n, double2** out, cudaStream_t s);
 cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tabA, float2* tabB,
                             cudaStream_t s);
 cudaError_t launch_stage_tw(float2* dst, int lgL, int count, cudaStream_t s);

@@ -20,11 +20,19 @@ struct cs_plan_s {
   cudaStream_t cap = nullptr;      // private stream used only for graph capture
   Geo gi{}, ga{};                  // real-FFT (N = n/2) and complex-n (N = n) geometry
   float2* W = nullptr;
-  uint32_t* mask = nullptr;
-  uint32_t* prefix = nullptr;
-  int32_t* pos = nullptr;
+  // Rows of Omega per geometry, in the tile order of its column pass.
+  struct Sel {
+    uint32_t* mask = nullptr;
+    uint32_t* prefix = nullptr;
+    int32_t* pos = nullptr;     // compact position of y[i]
+    float* ys = nullptr;        // compact y in tile order
+  } si, sa;                     // si: real-FFT geometry gi, sa: complex-n geometry ga
   int32_t* rows32 = nullptr;
-  float* ys = nullptr;
+  // Solver state in tile order (natural order only at the API boundary).
+  float* xi_t = nullptr;        // ISTA iterate (float2[n/2])
+  float* xt_i = nullptr;        // monitor ground truth, gi tile order (float2[n/2])
+  float* xt_a = nullptr;        // monitor ground truth, ga tile order
+  float *av = nullptr, *az = nullptr, *amu = nullptr, *anu = nullptr, *ax = nullptr;   // ADMM state
   double* partials = nullptr;
   double* stats = nullptr;
   int* status = nullptr;
@@ -114,7 +122,9 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_plan(cs_plan_s* p) {
   if (!p) return;
   for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
-  void* bufs[] = {p->W, p->mask, p->prefix, p->pos, p->rows32, p->ys, p->partials, p->stats, p->status,
+  void* bufs[] = {p->W, p->si.mask, p->si.prefix, p->si.pos, p->si.ys, p->sa.mask, p->sa.prefix, p->sa.pos,
+                  p->sa.ys, p->rows32, p->xi_t, p->xt_i, p->xt_a, p->av, p->az, p->amu, p->anu, p->ax,
+                  p->partials, p->stats, p->status,
                   p->ca, p->tab_ista, p->tab_ista_b, p->tab_admm_c, p->tab_admm_b, p->abs2, p->twi, p->twa,
                   p->dense, p->dense2, p->dense3};
   for (void* b : bufs)
@@ -131,9 +141,10 @@ KParams kparams(const cs_plan_s* p, const Geo& g, int flags) {
   KParams k;
   k.geo = g;
   k.pp.W = p->W;
-  k.pp.mask = p->mask;
-  k.pp.prefix = p->prefix;
-  k.pp.ys = p->ys;
+  const cs_plan_s::Sel& sel = (&g == &p->gi) ? p->si : p->sa;
+  k.pp.mask = sel.mask;
+  k.pp.prefix = sel.prefix;
+  k.pp.ys = sel.ys;
   k.pp.partials = p->partials;
   k.pp.stats = p->stats;
   k.pp.tab_ista = p->tab_ista;
@@ -368,11 +379,15 @@ cs_status cs_plan(cs_plan_t* out, int64_t n, int64_t m, const int64_t* rows, con
   const int maxctas = p->ga.col_ctas > p->gi.col_ctas ? p->ga.col_ctas : p->gi.col_ctas;
   const int64_t npart = (int64_t)maxctas * NSTAT > 256 ? (int64_t)maxctas * NSTAT : 256;
   CS_PLAN_TRY(dalloc(&p->W, n));
-  CS_PLAN_TRY(dalloc(&p->mask, words));
-  CS_PLAN_TRY(dalloc(&p->prefix, words));
-  CS_PLAN_TRY(dalloc(&p->pos, m));
+  for (cs_plan_s::Sel* sel : {&p->si, &p->sa}) {
+    CS_PLAN_TRY(dalloc(&sel->mask, words));
+    CS_PLAN_TRY(dalloc(&sel->prefix, words));
+    CS_PLAN_TRY(dalloc(&sel->pos, m));
+    CS_PLAN_TRY(dalloc(&sel->ys, m));
+  }
   CS_PLAN_TRY(dalloc(&p->rows32, m));
-  CS_PLAN_TRY(dalloc(&p->ys, m));
+  for (float** b : {&p->xi_t, &p->xt_i, &p->xt_a, &p->av, &p->az, &p->amu, &p->anu, &p->ax})
+    CS_PLAN_TRY(dalloc(b, n));
   CS_PLAN_TRY(dalloc(&p->partials, npart));
   CS_PLAN_TRY(dalloc(&p->stats, NSTAT));
   CS_PLAN_TRY(dalloc(&p->status, 1));
@@ -398,7 +413,8 @@ cs_status cs_plan(cs_plan_t* out, int64_t n, int64_t m, const int64_t* rows, con
   CS_PLAN_TRY(cudaMemcpyAsync(d_rows, rows, m * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CS_PLAN_TRY(cudaMemcpyAsync(d_c, c, n * sizeof(double), cudaMemcpyHostToDevice, s));
   CS_PLAN_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), s));
-  CS_PLAN_TRY(cudaMemsetAsync(p->mask, 0, words * sizeof(uint32_t), s));
+  CS_PLAN_TRY(cudaMemsetAsync(p->si.mask, 0, words * sizeof(uint32_t), s));
+  CS_PLAN_TRY(cudaMemsetAsync(p->sa.mask, 0, words * sizeof(uint32_t), s));
   CS_PLAN_TRY(cudaMemsetAsync(p->stats, 0, NSTAT * sizeof(double), s));
   CS_PLAN_TRY(make_tables(p->gi, p->twi, s));
   CS_PLAN_TRY(make_tables(p->ga, p->twa, s));
@@ -409,12 +425,15 @@ cs_status cs_plan(cs_plan_t* out, int64_t n, int64_t m, const int64_t* rows, con
   CS_PLAN_TRY(launch_tab_admm_b(p->abs2, (int)tab_count(p->ga), n, 1.0, 1.0, p->tab_admm_b, s));
   p->b_rho = 1.0;
   p->b_sigma = 1.0;
-  CS_PLAN_TRY(launch_build_mask(d_rows, m, n, p->mask, p->status, s));
-  CS_PLAN_TRY(launch_prefix(p->mask, words, p->prefix, s));
+  CS_PLAN_TRY(launch_build_mask(d_rows, m, n, p->gi, 1, p->si.mask, p->status, s));
+  CS_PLAN_TRY(launch_build_mask(d_rows, m, n, p->ga, 0, p->sa.mask, p->status, s));
+  CS_PLAN_TRY(launch_prefix(p->si.mask, words, p->si.prefix, s));
+  CS_PLAN_TRY(launch_prefix(p->sa.mask, words, p->sa.prefix, s));
   CS_PLAN_TRY(cudaMemcpyAsync(p->host_status, p->status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CS_PLAN_TRY(cudaStreamSynchronize(s));
   if (*p->host_status & (STS_BAD_ROW | STS_DUP_ROW)) return fail(CS_ERR_ARG);
-  CS_PLAN_TRY(launch_row_pos(d_rows, m, p->mask, p->prefix, p->pos, p->rows32, s));
+  CS_PLAN_TRY(launch_row_pos(d_rows, m, p->gi, 1, p->si.mask, p->si.prefix, p->si.pos, p->rows32, s));
+  CS_PLAN_TRY(launch_row_pos(d_rows, m, p->ga, 0, p->sa.mask, p->sa.prefix, p->sa.pos, nullptr, s));
   CS_PLAN_TRY(cudaStreamSynchronize(s));
 #undef CS_PLAN_TRY
   cudaFree(d_rows);
@@ -508,6 +527,8 @@ cs_status cs_set_monitor(cs_plan_t p, const float* x_true, double nmse_tol, int 
   p->xtrue2 = 0.0;
   if (x_true) {
     CS_TRY(launch_norm2(x_true, p->n, p->partials, p->stats + ST_ERR2, p->stream));
+    CS_TRY(launch_to_tile(x_true, p->xt_i, p->gi, 1, p->stream));
+    CS_TRY(launch_to_tile(x_true, p->xt_a, p->ga, 0, p->stream));
     CS_TRY(read_back(p));
     p->xtrue2 = p->host_stats[ST_ERR2];
     if (!(p->xtrue2 > 0.0)) {
@@ -525,22 +546,25 @@ cs_status cs_ista(cs_plan_t p, const float* y, float lambda, float tau, int iter
   cudaStream_t s = p->stream;
   if (stats) CS_TRY(cudaEventRecord(p->ev0, s));
   CallArgs a{};
-  a.src = x;
-  a.x = x;
-  a.xtrue = p->xtrue;
+  a.src = x;             // the prologue transforms x(0) in natural order
+  a.x = p->xi_t;         // the iterate lives in tile order during the solve
+  a.xtrue = p->xtrue ? p->xt_i : nullptr;
   a.thr = (float)((double)tau * (double)lambda);
   a.tau = tau;
   p->launches = 0;
   CS_TRY(launch_set_args(a, p->ca, s));
-  CS_TRY(launch_scatter_y(y, p->pos, p->m, p->ys, p->status, s));
+  CS_TRY(launch_scatter_y(y, p->si.pos, p->m, p->si.ys, p->status, s));
   p->launches += 2;
   p->ista_args = true;
   p->admm_args = false;
   int run = 0, conv = 0;
   if (iters > 0) {
+    CS_TRY(launch_to_tile(x, p->xi_t, p->gi, 1, s));
     CS_TRY(launch_col(COL_LOAD, kparams(p, p->gi, 0), s));
-    p->launches += 1;
+    p->launches += 2;
     CS_TRY(solve_loop(p, K_ISTA, iters, &run, &conv, stats != nullptr));
+    CS_TRY(launch_from_tile(p->xi_t, x, p->gi, 1, s));
+    p->launches += 1;
   }
   if (stats) {
     CS_TRY(cudaEventRecord(p->ev1, s));
@@ -557,24 +581,29 @@ cs_status cs_ista(cs_plan_t p, const float* y, float lambda, float tau, int iter
   return CS_OK;
 }
 
-cs_status cs_admm_ex(cs_plan_t p, const float* y, float lambda, const cs_admm_params* prm, int iters, int warm,
-                     float* x, float* z, float* mu, float* nu, float* v, cs_stats* stats) {
-  if (!p || !y || !prm || !z || !mu || !nu || !v || !(lambda >= 0.f) || iters < 0 || !std::isfinite(lambda))
-    return CS_ERR_ARG;
-  if (!(prm->sigma > 0.0) || !(prm->rho > 0.0) || !(prm->tau1 > 0.0) || !(prm->tau2 > 0.0) ||
-      !std::isfinite(prm->sigma) || !std::isfinite(prm->rho) || !std::isfinite(prm->tau1) ||
-      !std::isfinite(prm->tau2))
-    return CS_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// Algorithm 3 on the plan's tile-ordered state.  Natural-order state pointers
+// may be null (then that vector is neither read nor returned); warm reads
+// v, z, mu, nu (all non-null) as the starting state.
+cs_status admm_impl(cs_plan_t p, const float* y, float lambda, const cs_admm_params* prm, int iters, int warm,
+                    float* x, float* z, float* mu, float* nu, float* v, cs_stats* stats) {
   cudaStream_t s = p->stream;
   if (stats) CS_TRY(cudaEventRecord(p->ev0, s));
   const size_t nb = p->n * sizeof(float);
-  if (!warm) {
-    CS_TRY(cudaMemsetAsync(v, 0, nb, s));
-    CS_TRY(cudaMemsetAsync(z, 0, nb, s));
-    CS_TRY(cudaMemsetAsync(mu, 0, nb, s));
-    CS_TRY(cudaMemsetAsync(nu, 0, nb, s));
-  }
   p->launches = 0;
+  float* tiled[4] = {p->av, p->az, p->amu, p->anu};
+  float* natural[4] = {v, z, mu, nu};
+  for (int i = 0; i < 4; ++i) {
+    if (warm) {
+      CS_TRY(launch_to_tile(natural[i], tiled[i], p->ga, 0, s));
+      p->launches += 1;
+    } else {
+      CS_TRY(cudaMemsetAsync(tiled[i], 0, nb, s));
+    }
+  }
   if (prm->rho != p->b_rho || prm->sigma != p->b_sigma) {
     CS_TRY(launch_tab_admm_b(p->abs2, (int)tab_count(p->ga), p->n, prm->rho, prm->sigma, p->tab_admm_b, s));
     p->launches += 1;
@@ -582,12 +611,12 @@ cs_status cs_admm_ex(cs_plan_t p, const float* y, float lambda, const cs_admm_pa
     p->b_sigma = prm->sigma;
   }
   CallArgs a{};
-  a.x = x;
-  a.z = z;
-  a.mu = mu;
-  a.nu = nu;
-  a.v = v;
-  a.xtrue = p->xtrue;
+  a.x = p->ax;
+  a.z = p->az;
+  a.mu = p->amu;
+  a.nu = p->anu;
+  a.v = p->av;
+  a.xtrue = p->xtrue ? p->xt_a : nullptr;
   a.thr = (float)((double)lambda / prm->sigma);
   a.rho = (float)prm->rho;
   a.sigma = (float)prm->sigma;
@@ -596,7 +625,7 @@ cs_status cs_admm_ex(cs_plan_t p, const float* y, float lambda, const cs_admm_pa
   a.d_on = (float)(1.0 / (1.0 + prm->rho));
   a.d_off = (float)(1.0 / prm->rho);
   CS_TRY(launch_set_args(a, p->ca, s));
-  CS_TRY(launch_scatter_y(y, p->pos, p->m, p->ys, p->status, s));
+  CS_TRY(launch_scatter_y(y, p->sa.pos, p->m, p->sa.ys, p->status, s));
   p->launches += 2;
   p->admm_args = true;
   p->ista_args = false;
@@ -606,6 +635,14 @@ cs_status cs_admm_ex(cs_plan_t p, const float* y, float lambda, const cs_admm_pa
     p->launches += 1;
     CS_TRY(solve_loop(p, K_ADMM, iters, &run, &conv, stats != nullptr));
   }
+  float* outs_t[5] = {p->av, p->az, p->amu, p->anu, p->ax};
+  float* outs_n[5] = {v, z, mu, nu, iters > 0 ? x : nullptr};
+  for (int i = 0; i < 5; ++i) {
+    if (!outs_n[i]) continue;
+    CS_TRY(launch_from_tile(outs_t[i], outs_n[i], p->ga, 0, s));
+    p->launches += 1;
+  }
+  if (x && iters == 0) CS_TRY(cudaMemsetAsync(x, 0, nb, s));
   if (stats) {
     CS_TRY(cudaEventRecord(p->ev1, s));
     CS_TRY(cudaMemcpyAsync(p->host_status, p->status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -618,6 +655,21 @@ cs_status cs_admm_ex(cs_plan_t p, const float* y, float lambda, const cs_admm_pa
     return latched_status(p);
   }
   return CS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cs_status cs_admm_ex(cs_plan_t p, const float* y, float lambda, const cs_admm_params* prm, int iters, int warm,
+                     float* x, float* z, float* mu, float* nu, float* v, cs_stats* stats) {
+  if (!p || !y || !prm || !z || !mu || !nu || !v || !(lambda >= 0.f) || iters < 0 || !std::isfinite(lambda))
+    return CS_ERR_ARG;
+  if (!(prm->sigma > 0.0) || !(prm->rho > 0.0) || !(prm->tau1 > 0.0) || !(prm->tau2 > 0.0) ||
+      !std::isfinite(prm->sigma) || !std::isfinite(prm->rho) || !std::isfinite(prm->tau1) ||
+      !std::isfinite(prm->tau2))
+    return CS_ERR_ARG;
+  return admm_impl(p, y, lambda, prm, iters, warm, x, z, mu, nu, v, stats);
 }
 
 cs_status cs_profile_pass(cs_plan_t p, int pass_id, int reps) {
@@ -641,8 +693,8 @@ cs_status cs_profile_pass(cs_plan_t p, int pass_id, int reps) {
 cs_status cs_admm(cs_plan_t p, const float* y, float lambda, float rho, int iters, float* z, cs_stats* stats) {
   if (!p || !y || !z || !(rho > 0.f) || !(lambda >= 0.f) || iters < 0) return CS_ERR_ARG;
   cs_admm_params prm{rho, rho, 1.0, 1.0};
-  // the state of Algorithm 3 lives in plan scratch; only z is returned
-  return cs_admm_ex(p, y, lambda, &prm, iters, 0, nullptr, z, p->dense2, p->dense3, p->dense, stats);
+  // zero start; only z is returned
+  return admm_impl(p, y, lambda, &prm, iters, 0, nullptr, z, nullptr, nullptr, nullptr, stats);
 }
 
 }  // extern "C"

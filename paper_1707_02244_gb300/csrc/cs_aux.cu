@@ -139,15 +139,44 @@ __global__ void tab_admm_b_k(const double* __restrict__ abs2, int64_t count, int
   tabb[t] = (float)(1.0 / ((double)n * (rho * abs2[t] + sigma)));
 }
 
-__global__ void build_mask_k(const int64_t* __restrict__ rows, int64_t m, int64_t n, uint32_t* mask,
-                             int* status) {
+// Tile-order position of natural index p in the column-pass layout of g:
+// p = gi G + c + j2 N1  ->  t = gi (G N2) + j2 G + c.
+__device__ __forceinline__ int64_t nat_to_tile(const Geo& g, int64_t p) {
+  const int64_t j1 = p & (g.N1 - 1), j2 = p >> g.lgN1;
+  return ((j1 >> g.lgG) << (g.lgG + g.lgN2)) + (j2 << g.lgG) + (j1 & (g.G - 1));
+}
+__device__ __forceinline__ int64_t tile_to_nat(const Geo& g, int64_t t) {
+  const int64_t gi = t >> (g.lgG + g.lgN2), rem = t & ((int64_t(1) << (g.lgG + g.lgN2)) - 1);
+  return (gi << g.lgG) + (rem & (g.G - 1)) + ((rem >> g.lgG) << g.lgN1);
+}
+// Bit of spatial row r in the tile-ordered row mask: in the real-FFT
+// geometry rows 2p and 2p+1 share complex element p.
+__device__ __forceinline__ int64_t row_bit(const Geo& g, int packed, int64_t r) {
+  return packed ? 2 * nat_to_tile(g, r >> 1) + (r & 1) : nat_to_tile(g, r);
+}
+
+__global__ void build_mask_k(const int64_t* __restrict__ rows, int64_t m, int64_t n, Geo g, int packed,
+                             uint32_t* mask, int* status) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
   const int64_t r = rows[i];
   if (r < 0 || r >= n) { atomicOr(status, STS_BAD_ROW); return; }
-  const uint32_t bit = 1u << (r & 31);
-  const uint32_t old = atomicOr(mask + (r >> 5), bit);
+  const int64_t b = row_bit(g, packed, r);
+  const uint32_t bit = 1u << (b & 31);
+  const uint32_t old = atomicOr(mask + (b >> 5), bit);
   if (old & bit) atomicOr(status, STS_DUP_ROW);
+}
+
+template <typename T>
+__global__ void to_tile_k(const T* __restrict__ nat, T* __restrict__ tiled, Geo g) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < g.N) tiled[t] = nat[tile_to_nat(g, t)];
+}
+
+template <typename T>
+__global__ void from_tile_k(const T* __restrict__ tiled, T* __restrict__ nat, Geo g) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < g.N) nat[tile_to_nat(g, t)] = tiled[t];
 }
 
 // Exclusive prefix count of set bits per 32-bit word, one CTA.
@@ -169,15 +198,18 @@ __global__ void __launch_bounds__(1024) prefix_k(const uint32_t* __restrict__ ma
   for (int64_t w = lo; w < hi; ++w) { prefix[w] = acc; acc += __popc(mask[w]); }
 }
 
-__global__ void row_pos_k(const int64_t* __restrict__ rows, int64_t m, const uint32_t* __restrict__ mask,
-                          const uint32_t* __restrict__ prefix, int32_t* __restrict__ pos,
-                          int32_t* __restrict__ rows32) {
+// pos[i] = rank of row rows[i] among the kept rows in tile order (index of
+// y[i] in the compact tile-ordered y); rows32 = rows as int32.
+__global__ void row_pos_k(const int64_t* __restrict__ rows, int64_t m, Geo g, int packed,
+                          const uint32_t* __restrict__ mask, const uint32_t* __restrict__ prefix,
+                          int32_t* __restrict__ pos, int32_t* __restrict__ rows32) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
   const int64_t r = rows[i];
-  const uint32_t w = mask[r >> 5];
-  pos[i] = (int32_t)(prefix[r >> 5] + __popc(w & ((1u << (r & 31)) - 1u)));
-  rows32[i] = (int32_t)r;
+  const int64_t b = row_bit(g, packed, r);
+  const uint32_t w = mask[b >> 5];
+  pos[i] = (int32_t)(prefix[b >> 5] + __popc(w & ((1u << (b & 31)) - 1u)));
+  if (rows32) rows32[i] = (int32_t)r;
 }
 
 __global__ void scatter_y_k(const float* __restrict__ y, const int32_t* __restrict__ pos, int64_t m,
@@ -311,9 +343,25 @@ cudaError_t launch_tab_admm_b(const double* abs2, int count, int64_t n, double r
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_mask(const int64_t* rows, int64_t m, int64_t n, uint32_t* mask, int* status,
-                              cudaStream_t s) {
-  build_mask_k<<<blocks_for(m), AUX_NT, 0, s>>>(rows, m, n, mask, status);
+cudaError_t launch_build_mask(const int64_t* rows, int64_t m, int64_t n, const Geo& g, int packed,
+                              uint32_t* mask, int* status, cudaStream_t s) {
+  build_mask_k<<<blocks_for(m), AUX_NT, 0, s>>>(rows, m, n, g, packed, mask, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_tile(const void* nat, void* tiled, const Geo& g, int complex_elems, cudaStream_t s) {
+  if (complex_elems)
+    to_tile_k<float2><<<blocks_for(g.N), AUX_NT, 0, s>>>((const float2*)nat, (float2*)tiled, g);
+  else
+    to_tile_k<float><<<blocks_for(g.N), AUX_NT, 0, s>>>((const float*)nat, (float*)tiled, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_tile(const void* tiled, void* nat, const Geo& g, int complex_elems, cudaStream_t s) {
+  if (complex_elems)
+    from_tile_k<float2><<<blocks_for(g.N), AUX_NT, 0, s>>>((const float2*)tiled, (float2*)nat, g);
+  else
+    from_tile_k<float><<<blocks_for(g.N), AUX_NT, 0, s>>>((const float*)tiled, (float*)nat, g);
   return cudaGetLastError();
 }
 
@@ -322,9 +370,9 @@ cudaError_t launch_prefix(const uint32_t* mask, int64_t words, uint32_t* prefix,
   return cudaGetLastError();
 }
 
-cudaError_t launch_row_pos(const int64_t* rows, int64_t m, const uint32_t* mask, const uint32_t* prefix,
-                           int32_t* pos, int32_t* rows32, cudaStream_t s) {
-  row_pos_k<<<blocks_for(m), AUX_NT, 0, s>>>(rows, m, mask, prefix, pos, rows32);
+cudaError_t launch_row_pos(const int64_t* rows, int64_t m, const Geo& g, int packed, const uint32_t* mask,
+                           const uint32_t* prefix, int32_t* pos, int32_t* rows32, cudaStream_t s) {
+  row_pos_k<<<blocks_for(m), AUX_NT, 0, s>>>(rows, m, g, packed, mask, prefix, pos, rows32);
   return cudaGetLastError();
 }
 

@@ -27,8 +27,11 @@ struct EpiHook {
   Acc& acc;
   __device__ __forceinline__ void begin(int, int) {}
   __device__ __forceinline__ float2 pre(int, int, int, int, float2 v) const { return v; }
+  int tbase;   // tile-order index of this CTA's first element: col0 * N2
+  int lgG;
   __device__ __forceinline__ float2 post(int vec, int j, int r, int lgLR, float2 v) {
-    return Epi<KIND>::apply(kp, a, v, col0 + vec + ((j + (r << lgLR)) << lgN1), acc);
+    const int idx = j + (r << lgLR);
+    return Epi<KIND>::apply(kp, a, v, col0 + vec + (idx << lgN1), tbase + (idx << lgG) + vec, acc);
   }
 };
 
@@ -56,8 +59,8 @@ __global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB) col_kernel(const KPa
   using E = Epi<KIND>;
   using S = ColShape<SHAPE>;
   extern __shared__ float2 sm[];
+  pdl_trigger();
   const Geo& g = kp.geo;
-  const CallArgs a = *kp.ca;
   const int lgG = S::lgG(g), lgN2 = S::lgN2(g);
   const int G = 1 << lgG;
   const int col0 = blockIdx.x << lgG;
@@ -67,7 +70,9 @@ __global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB) col_kernel(const KPa
   constexpr int TW_N = TWS ? stage_tw_count(10) : 2;
   __shared__ __align__(16) float2 tws[TW_N];
   const float2* tw = TWS ? tws : g.tw2;
-  if (TWS) copy_table<NT>(tws, g.tws2, TW_N);
+  if (TWS) copy_table<NT>(tws, g.tws2, TW_N);   // plan constant
+  pdl_wait();                                   // everything below may depend on earlier kernels
+  const CallArgs a = *kp.ca;
   float2* __restrict__ W = kp.pp.W;
   Acc acc;
   acc.zero();
@@ -91,12 +96,12 @@ __global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB) col_kernel(const KPa
       }
     }
     __syncthreads();
-    EpiHook<KIND> hook{kp, a, col0, g.lgN1, acc};
+    EpiHook<KIND> hook{kp, a, col0, g.lgN1, acc, col0 << lgN2, lgG};
     tile_fft<+1, TILE, NT, TWS>(sm, lay, tw, lgN2, hook);
   } else {
     for (int e = threadIdx.x; e < tot; e += NT) {
       const int j2 = e >> lgG, c = e & (G - 1);
-      sm[pad(e)] = E::apply(kp, a, make_float2(0.f, 0.f), col0 + c + (j2 << g.lgN1), acc);
+      sm[pad(e)] = E::apply(kp, a, make_float2(0.f, 0.f), col0 + c + (j2 << g.lgN1), (col0 << lgN2) + e, acc);
     }
     __syncthreads();
   }

@@ -141,6 +141,16 @@ struct StaticLayout {
   __device__ __forceinline__ int at(int vec, int idx) const {
     return VEC_FAST ? ((idx << LGNV) + vec) : ((vec << LGL) + idx);
   }
+  // Padded index split: pad(at(vec, idx)) = padV(vec) + padP(idx), and
+  // padP(a + b) = padP(a) + padP(b) whenever b (or a) times the element
+  // stride is a multiple of 16 -- so a stage's 16 reads / writes are one base
+  // plus compile-time offsets.  (Cols: vec < 2^LGNV <= 16 never carries.)
+  __device__ __forceinline__ static constexpr int padP(int idx) {
+    return VEC_FAST ? ((idx << LGNV) + ((idx << LGNV) >> 4)) : (idx + (idx >> 4));
+  }
+  __device__ __forceinline__ static constexpr int padV(int vec) {
+    return VEC_FAST ? vec : vec * ((1 << LGL) + (1 << (LGL - 4)));
+  }
 };
 
 // Element hooks: `pre` runs on the values a first stage loads (before its
@@ -182,8 +192,14 @@ __device__ __forceinline__ void stockham_stage(float2* s, const LAY& lay, int lg
     if (lay.VF()) { vecs[i] = b & ((1 << lgnv) - 1); js[i] = b >> lgnv; }
     else { vecs[i] = b >> lgLR; js[i] = b & ((1 << lgLR) - 1); }
     if (b < nb) {
+      if constexpr (LAY::kStatic) {
+        const float2* lb = s + LAY::padV(vecs[i]) + LAY::padP(js[i]);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = s[pad(lay.at(vecs[i], js[i] + (r << lgLR)))];
+        for (int r = 0; r < R; ++r) v[i][r] = lb[LAY::padP(r << lgLR)];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i][r] = s[pad(lay.at(vecs[i], js[i] + (r << lgLR)))];
+      }
     }
   }
   __syncthreads();
@@ -210,11 +226,16 @@ __device__ __forceinline__ void stockham_stage(float2* s, const LAY& lay, int lg
       dft<R, DIR>(v[i]);
       const int base = ((j - k) << lgR) + k;   // in the last stage base == j, Ls == L/R
       if (H::kPost && last && !(H::kPre && first)) hook.begin(vecs[i], j);
+      // static layouts: Ls * stride is a multiple of 16 past the first stage,
+      // and in the first stage base = 16 j is (radix 16), so the split holds
+      float2* sb = s;
+      if constexpr (LAY::kStatic) sb = s + LAY::padV(vecs[i]) + LAY::padP(base);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         float2 o = v[i][out_slot<R>(r)];
         if (H::kPost && last) o = hook.post(vecs[i], j, r, lgLR, o);
-        s[pad(lay.at(vecs[i], base + r * Ls))] = o;
+        if constexpr (LAY::kStatic) sb[LAY::padP(r * Ls)] = o;
+        else s[pad(lay.at(vecs[i], base + r * Ls))] = o;
       }
     }
   }

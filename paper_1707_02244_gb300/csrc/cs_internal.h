@@ -42,9 +42,9 @@ enum : int {
 // Plan-constant device pointers, passed by value to every pass kernel.
 struct PlanPtrs {
   float2* W;                 // exchange buffer, complex[n]
-  const uint32_t* mask;      // bit r set iff row r is in Omega, [n/32]
+  const uint32_t* mask;      // rows of Omega, one bit per row in tile order, [n/32]
   const uint32_t* prefix;    // set bits before word w, [n/32]
-  const float* ys;           // y in ascending-row order, [m]
+  const float* ys;           // y in tile order of its rows, [m]
   double* partials;          // [max_ctas * NSTAT]
   double* stats;             // [NSTAT] finalised sums
   const float4* tab_ista;    // (a, a') per pair slot, real-FFT geometry
@@ -121,13 +121,19 @@ cudaError_t launch_tab_admm(const double2* chat, const Geo& g, int64_t n, float2
                             double* abs2, cudaStream_t s);
 cudaError_t launch_tab_admm_b(const double* abs2, int count, int64_t n, double rho,
                               double sigma, float* tabb, cudaStream_t s);
-cudaError_t launch_build_mask(const int64_t* rows, int64_t m, int64_t n, uint32_t* mask,
-                              int* status, cudaStream_t s);
+// Row mask of Omega in the tile order of geometry g (packed: two spatial rows
+// per complex element, the real-FFT geometry).
+cudaError_t launch_build_mask(const int64_t* rows, int64_t m, int64_t n, const Geo& g, int packed,
+                              uint32_t* mask, int* status, cudaStream_t s);
+// Natural order <-> tile order of the column pass (float2 elements when
+// complex_elems, else float), g.N elements.
+cudaError_t launch_to_tile(const void* nat, void* tiled, const Geo& g, int complex_elems, cudaStream_t s);
+cudaError_t launch_from_tile(const void* tiled, void* nat, const Geo& g, int complex_elems, cudaStream_t s);
 cudaError_t launch_prefix(const uint32_t* mask, int64_t words, uint32_t* prefix,
                           cudaStream_t s);
-cudaError_t launch_row_pos(const int64_t* rows, int64_t m, const uint32_t* mask,
-                           const uint32_t* prefix, int32_t* pos, int32_t* rows32,
-                           cudaStream_t s);
+cudaError_t launch_row_pos(const int64_t* rows, int64_t m, const Geo& g, int packed,
+                           const uint32_t* mask, const uint32_t* prefix, int32_t* pos,
+                           int32_t* rows32, cudaStream_t s);
 cudaError_t launch_scatter_y(const float* y, const int32_t* pos, int64_t m, float* ys,
                              int* status, cudaStream_t s);
 cudaError_t launch_gather_rows(const float* dense, const int32_t* rows32, int64_t m,

@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
   constexpr int NLD = Cfg<TILE>::NLD;
   using S = MidShape<SHAPE>;
   extern __shared__ float2 sm[];
+  pdl_trigger();
   const Geo& g = kp.geo;
   const int lgU = S::lgU(g), U = 1 << lgU;
   const int u0 = blockIdx.x << lgU;
@@ -178,6 +179,7 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
       rt[which][tt] = r < (1 << lgR) ? tw4(g, ((r << (lgN1 - lgR)) * k2) & (g.N - 1)) : make_float2(1.f, 0.f);
     }
   }
+  pdl_wait();   // the twiddle tables above are plan constants; W is not
   {
     float4 buf[NLD];
 #pragma unroll

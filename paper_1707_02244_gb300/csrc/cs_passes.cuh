@@ -91,21 +91,28 @@ __device__ __forceinline__ float2 ld2(const float* p, int i) {
 }
 
 // ---------------------------------------------------------------- epilogues
-// apply(v, p, acc): v is the inverse-FFT output at complex index p (when the
+// apply(v, p, t, acc): v is the inverse-FFT output at complex index p (when the
 // kind reads the exchange buffer); returns the forward-FFT input at p.
 
+// Index conventions.  p is the natural index (complex p of the packed vector
+// in the real-FFT geometry, the spatial index in the complex-n geometry);
+// API-facing buffers (src, dst, aux) use it.  t is the tile-order index of
+// the column pass: t = g (G N2) + j2 G + c for p = g G + c + j2 N1.  The
+// solver state (x; v, z, mu, nu), the ground truth copy, the row mask and the
+// compact y all live in tile order, so each column CTA touches one contiguous
+// block of every one of them.
 template <int KIND> struct Epi;
 
 template <> struct Epi<COL_LOAD> {
   static constexpr bool kRead = false, kFwd = true;
-  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2, int p, Acc&) {
+  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2, int p, int t, Acc&) {
     return ld2(a.src, p);
   }
 };
 
 template <> struct Epi<COL_LOAD_SCALED> {
   static constexpr bool kRead = false, kFwd = true;
-  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2, int p, Acc&) {
+  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2, int p, int t, Acc&) {
     const float s = (float)rsqrt(kp.pp.stats[ST_X2]);
     float2 u = cscale(ld2(a.src, p), s);
     reinterpret_cast<float2*>(a.aux)[p] = u;
@@ -115,7 +122,7 @@ template <> struct Epi<COL_LOAD_SCALED> {
 
 template <> struct Epi<COL_STORE> {
   static constexpr bool kRead = true, kFwd = false;
-  __device__ static float2 apply(const KParams&, const CallArgs& a, float2 v, int p, Acc&) {
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2 v, int p, int t, Acc&) {
     reinterpret_cast<float2*>(a.dst)[p] = v;
     return v;
   }
@@ -123,10 +130,10 @@ template <> struct Epi<COL_STORE> {
 
 template <> struct Epi<COL_MASK> {
   static constexpr bool kRead = true, kFwd = true;
-  __device__ static float2 apply(const KParams& kp, const CallArgs&, float2 v, int p, Acc&) {
+  __device__ static float2 apply(const KParams& kp, const CallArgs&, float2 v, int p, int t, Acc&) {
     RowSel rs{kp.pp.mask, kp.pp.prefix};
     int i0;
-    const uint32_t mm = rs.get2(p, i0);
+    const uint32_t mm = rs.get2(t, i0);
     return make_float2((mm & 1u) ? v.x : 0.f, (mm & 2u) ? v.y : 0.f);
   }
 };
@@ -135,10 +142,10 @@ template <> struct Epi<COL_MASK> {
 // them, so that the next product gives A^T r = C^T P^T r.
 template <> struct Epi<COL_RESIDUAL> {
   static constexpr bool kRead = true, kFwd = true;
-  __device__ static float2 apply(const KParams& kp, const CallArgs&, float2 v, int p, Acc& acc) {
+  __device__ static float2 apply(const KParams& kp, const CallArgs&, float2 v, int p, int t, Acc& acc) {
     RowSel rs{kp.pp.mask, kp.pp.prefix};
     int i0;
-    const uint32_t mm = rs.get2(p, i0);
+    const uint32_t mm = rs.get2(t, i0);
     const float r0 = (mm & 1u) ? __ldg(kp.pp.ys + i0) - v.x : 0.f;
     const float r1 = (mm & 2u) ? __ldg(kp.pp.ys + i0 + (int)(mm & 1u)) - v.y : 0.f;
     acc.v[ST_R2] = fmaf(r0, r0, fmaf(r1, r1, acc.v[ST_R2]));
@@ -147,23 +154,27 @@ template <> struct Epi<COL_RESIDUAL> {
 };
 
 // x(t) = eta_{tau lambda}[x(t-1) + tau A^T r(t)]  (Algorithm 1, Eq. 4)
+// Every element of x is read once, by the thread that then overwrites it, and
+// by no other thread: the read can take the read-only path, which lets the
+// loads of a thread's elements issue together instead of waiting behind the
+// stores to x (that might otherwise alias them).
 template <bool FWD> struct EpiIsta {
   static constexpr bool kRead = true, kFwd = FWD;
-  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2 g, int p, Acc& acc) {
+  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2 g, int p, int t, Acc& acc) {
     float2* x = reinterpret_cast<float2*>(a.x);
-    const float2 xo = x[p];
+    const float2 xo = __ldg(x + t);
     float2 xn;
     xn.x = soft(fmaf(a.tau, g.x, xo.x), a.thr);
     xn.y = soft(fmaf(a.tau, g.y, xo.y), a.thr);
-    x[p] = xn;
+    x[t] = xn;
     if (kp.flags & FL_STATS) {
       const float d0 = xn.x - xo.x, d1 = xn.y - xo.y;
       acc.v[ST_DX2] = fmaf(d0, d0, fmaf(d1, d1, acc.v[ST_DX2]));
       acc.v[ST_X2] = fmaf(xn.x, xn.x, fmaf(xn.y, xn.y, acc.v[ST_X2]));
       acc.v[ST_L1] += fabsf(xo.x) + fabsf(xo.y);
       if (a.xtrue) {
-        const float2 t = ld2(a.xtrue, p);
-        const float e0 = xn.x - t.x, e1 = xn.y - t.y;
+        const float2 xs = ld2(a.xtrue, t);
+        const float e0 = xn.x - xs.x, e1 = xn.y - xs.y;
         acc.v[ST_ERR2] = fmaf(e0, e0, fmaf(e1, e1, acc.v[ST_ERR2]));
       }
       if (!isfinite(xn.x) || !isfinite(xn.y)) acc.v[ST_NONFIN] += 1.f;
@@ -176,7 +187,7 @@ template <> struct Epi<COL_ISTA_LAST> : EpiIsta<false> {};
 
 template <> struct Epi<COL_POWER_OUT> {
   static constexpr bool kRead = true, kFwd = false;
-  __device__ static float2 apply(const KParams&, const CallArgs& a, float2 w, int p, Acc& acc) {
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2 w, int p, int t, Acc& acc) {
     const float2 u = ld2(a.aux, p);
     reinterpret_cast<float2*>(a.dst)[p] = w;
     acc.v[ST_X2] = fmaf(w.x, w.x, fmaf(w.y, w.y, acc.v[ST_X2]));
@@ -188,8 +199,8 @@ template <> struct Epi<COL_POWER_OUT> {
 // Complex-n geometry: p is the spatial index itself.
 template <> struct Epi<COL_ADMM_INIT> {
   static constexpr bool kRead = false, kFwd = true;
-  __device__ static float2 apply(const KParams&, const CallArgs& a, float2, int p, Acc&) {
-    return make_float2(a.v[p], a.z[p] - a.nu[p]);
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2, int p, int t, Acc&) {
+    return make_float2(__ldg(a.v + t), __ldg(a.z + t) - __ldg(a.nu + t));
   }
 };
 
@@ -198,29 +209,30 @@ template <> struct Epi<COL_ADMM_INIT> {
 // v <- v + mu; the next x-update reads (v) + i (z - nu).
 template <bool FWD> struct EpiAdmm {
   static constexpr bool kRead = true, kFwd = FWD;
-  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2 xc, int p, Acc& acc) {
+  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2 xc, int p, int t, Acc& acc) {
     RowSel rs{kp.pp.mask, kp.pp.prefix};
     int iy;
-    const bool on = rs.get(p, iy);
+    const bool on = rs.get(t, iy);
     const float yv = on ? __ldg(kp.pp.ys + iy) : 0.f;
     const float x = xc.x, cx = xc.y;
-    const float mu = a.mu[p], nu = a.nu[p];
+    // read-once / write-once per element by its own thread: read-only path (as EpiIsta)
+    const float mu = __ldg(a.mu + t), nu = __ldg(a.nu + t);
     const float d = on ? a.d_on : a.d_off;
     const float v = d * fmaf(a.rho, cx - mu, yv);
     const float z = soft(x + nu, a.thr);
     const float mu2 = fmaf(a.tau1, v - cx, mu);
     const float nu2 = fmaf(a.tau2, x - z, nu);
     const float vf = v + mu2;
-    a.mu[p] = mu2;
-    a.nu[p] = nu2;
+    a.mu[t] = mu2;
+    a.nu[t] = nu2;
     if (kp.flags & FL_WRITE_STATE) {
-      a.z[p] = z;
-      a.v[p] = vf;
-      if (a.x) a.x[p] = x;
+      a.z[t] = z;
+      a.v[t] = vf;
+      if (a.x) a.x[t] = x;
     }
     if (kp.flags & FL_STATS) {
       if (a.xtrue) {
-        const float e = z - __ldg(a.xtrue + p);
+        const float e = z - __ldg(a.xtrue + t);
         acc.v[ST_ERR2] = fmaf(e, e, acc.v[ST_ERR2]);
       }
       const float pr = x - z;
@@ -243,10 +255,28 @@ template <int TILE> struct Cfg {
   static constexpr int NLD = TILE / (2 * NT);           // float4 loads per thread per tile
 };
 
+// Programmatic dependent launch: every pass kernel lets the next kernel in the
+// stream start launching as soon as all of its own CTAs are running
+// (pdl_trigger at entry), and waits for the previous kernel to finish
+// (pdl_wait) only before its first read of data produced upstream; what it
+// does before that reads plan constants only.  Outside a programmatic launch
+// both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename K>
 cudaError_t launch_k(K kern, int grid, int tile, const KParams& kp, cudaStream_t s) {
-  kern<<<grid, tile / EPT, pass_smem_bytes(tile), s>>>(kp);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(tile / EPT);
+  cfg.dynamicSmemBytes = pass_smem_bytes(tile);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, kp);
 }
 
 // Opt a kernel into its dynamic shared memory and ask for a carveout just

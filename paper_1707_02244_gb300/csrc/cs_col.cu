@@ -71,11 +71,27 @@ __global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB) col_kernel(const KPa
   __shared__ __align__(16) float2 tws[TW_N];
   const float2* tw = TWS ? tws : g.tw2;
   if (TWS) copy_table<NT>(tws, g.tws2, TW_N);   // plan constant
+  // the tile's row-mask and prefix words (plan constants): 2 bits per element
+  // in the packed geometry, 1 in complex-n
+  constexpr int MB = UsesMask<KIND>::kBits;
+  constexpr int MW = MB ? TILE * MB / 32 : 1;
+  __shared__ uint32_t smask[MW], spref[MW];
+  const int wbase = MB ? (((col0 << lgN2) * MB) >> 5) : 0;
+  if (MB) {
+    const int words = (tot * MB) >> 5;
+    for (int w = threadIdx.x; w < words; w += NT) {
+      smask[w] = __ldg(kp.pp.mask + wbase + w);
+      spref[w] = __ldg(kp.pp.prefix + wbase + w);
+    }
+  }
   pdl_wait();                                   // everything below may depend on earlier kernels
   const CallArgs a = *kp.ca;
   float2* __restrict__ W = kp.pp.W;
   Acc acc;
   acc.zero();
+  acc.smask = smask;
+  acc.spref = spref;
+  acc.wbase = wbase;
 
   if (E::kRead) {
     float4 buf[NLD];

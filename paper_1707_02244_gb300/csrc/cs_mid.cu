@@ -97,15 +97,15 @@ __device__ __forceinline__ void op_real(const PlanPtrs& pp, int tidx, float2& za
 //   X = bhat (rho chat V + sigma Wk) / N            (x-update, Algorithm 3)
 //   Pc = conj(chat) X                                 (spectrum of C x)
 //   Z'_k = X + i Pc,  Z'_{N-k} = conj(X) + i conj(Pc)
-__device__ __forceinline__ void op_admm(const PlanPtrs& pp, const CallArgs& a, int tidx,
+__device__ __forceinline__ void op_admm(const PlanPtrs& pp, float rho, float sigma, int tidx,
                                         float2& za, float2& zb) {
   const float2 ch = __ldg(pp.tab_admm_c + tidx);
   const float bb = __ldg(pp.tab_admm_b + tidx);
   const float2 V = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
   const float2 Wk = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
   const float2 cv = cmul(ch, V);
-  const float2 X = make_float2(bb * fmaf(a.rho, cv.x, a.sigma * Wk.x),
-                               bb * fmaf(a.rho, cv.y, a.sigma * Wk.y));
+  const float2 X = make_float2(bb * fmaf(rho, cv.x, sigma * Wk.x),
+                               bb * fmaf(rho, cv.y, sigma * Wk.y));
   const float2 Pc = cmulc(X, ch);
   za = make_float2(X.x - Pc.y, X.y + Pc.x);
   zb = make_float2(X.x + Pc.y, Pc.x - X.y);
@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
     }
   }
   pdl_wait();   // the twiddle tables above are plan constants; W is not
+  const float a_rho = kp.ca->rho, a_sigma = kp.ca->sigma;   // ADMM only
   {
     float4 buf[NLD];
 #pragma unroll
@@ -210,7 +211,6 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
   }
 
   // spectrum operator over all (k, N-k) pairs held by this CTA
-  const CallArgs a = *kp.ca;
   const int nslots = (U << lgN1) + (u0 == 0 ? 1 : 0);
   const int base_u1 = ((g.N2 >> 1) - 1) << lgN1;   // table offset of unit 0
   for (int t = threadIdx.x; t < nslots; t += NT) {
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
       tidx = base_u1 + q;
     }
     float2 za = sm[pad(ea)], zb = sm[pad(eb)];
-    if (KIND == MID_ADMM) op_admm(kp.pp, a, tidx, za, zb);
+    if (KIND == MID_ADMM) op_admm(kp.pp, a_rho, a_sigma, tidx, za, zb);
     else op_real<KIND == MID_ADJ>(kp.pp, tidx, za, zb);
     sm[pad(eb)] = zb;   // self-pairs (ea == eb) keep the k-side value
     sm[pad(ea)] = za;

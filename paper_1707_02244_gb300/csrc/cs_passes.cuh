@@ -39,6 +39,11 @@ constexpr int NACC = ST_NONFIN + 1;   // accumulated statistic slots
 
 struct Acc {
   float v[NACC];
+  // the CTA's tile of the row mask and its prefix counts, copied to shared
+  // memory (indexed by global word minus wbase)
+  const uint32_t* smask;
+  const uint32_t* spref;
+  int wbase;
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int i = 0; i < NACC; ++i) v[i] = 0.f;
@@ -67,23 +72,32 @@ __device__ void block_stats(const Acc& a, double* partials) {
   }
 }
 
-// Row-of-Omega test and compact y index for spatial row i.
+// Row-of-Omega test and compact y index for the row with mask bit i (tile
+// order), from the CTA's copy of its mask words in shared memory.
 struct RowSel {
-  const uint32_t* __restrict__ mask;
-  const uint32_t* __restrict__ prefix;
+  const uint32_t* mask;     // shared: words wbase ..
+  const uint32_t* prefix;
+  int wbase;
   __device__ __forceinline__ bool get(int i, int& idx) const {
-    const uint32_t w = __ldg(mask + (i >> 5));
+    const uint32_t w = mask[(i >> 5) - wbase];
     const int b = i & 31;
-    idx = (int)__ldg(prefix + (i >> 5)) + __popc(w & ((1u << b) - 1u));
+    idx = (int)prefix[(i >> 5) - wbase] + __popc(w & ((1u << b) - 1u));
     return (w >> b) & 1u;
   }
-  // rows 2p and 2p+1 (same mask word): returns the two bits, idx of row 2p
+  // bits 2p and 2p+1 (same word): returns the two bits, idx of bit 2p
   __device__ __forceinline__ uint32_t get2(int p, int& idx) const {
-    const uint32_t w = __ldg(mask + (p >> 4));
+    const uint32_t w = mask[(p >> 4) - wbase];
     const int b = (2 * p) & 31;
-    idx = (int)__ldg(prefix + (p >> 4)) + __popc(w & ((1u << b) - 1u));
+    idx = (int)prefix[(p >> 4) - wbase] + __popc(w & ((1u << b) - 1u));
     return (w >> b) & 3u;
   }
+};
+
+// Which epilogues look up the row mask, and how many mask bits one element
+// of the tile holds (2 in the packed real-FFT geometry, 1 in complex-n).
+template <int KIND> struct UsesMask {
+  static constexpr int kBits = (KIND == COL_RESIDUAL || KIND == COL_MASK) ? 2
+                              : (KIND == COL_ADMM || KIND == COL_ADMM_LAST) ? 1 : 0;
 };
 
 __device__ __forceinline__ float2 ld2(const float* p, int i) {
@@ -130,8 +144,8 @@ template <> struct Epi<COL_STORE> {
 
 template <> struct Epi<COL_MASK> {
   static constexpr bool kRead = true, kFwd = true;
-  __device__ static float2 apply(const KParams& kp, const CallArgs&, float2 v, int p, int t, Acc&) {
-    RowSel rs{kp.pp.mask, kp.pp.prefix};
+  __device__ static float2 apply(const KParams& kp, const CallArgs&, float2 v, int p, int t, Acc& acc) {
+    RowSel rs{acc.smask, acc.spref, acc.wbase};
     int i0;
     const uint32_t mm = rs.get2(t, i0);
     return make_float2((mm & 1u) ? v.x : 0.f, (mm & 2u) ? v.y : 0.f);
@@ -143,7 +157,7 @@ template <> struct Epi<COL_MASK> {
 template <> struct Epi<COL_RESIDUAL> {
   static constexpr bool kRead = true, kFwd = true;
   __device__ static float2 apply(const KParams& kp, const CallArgs&, float2 v, int p, int t, Acc& acc) {
-    RowSel rs{kp.pp.mask, kp.pp.prefix};
+    RowSel rs{acc.smask, acc.spref, acc.wbase};
     int i0;
     const uint32_t mm = rs.get2(t, i0);
     const float r0 = (mm & 1u) ? __ldg(kp.pp.ys + i0) - v.x : 0.f;
@@ -210,7 +224,7 @@ template <> struct Epi<COL_ADMM_INIT> {
 template <bool FWD> struct EpiAdmm {
   static constexpr bool kRead = true, kFwd = FWD;
   __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2 xc, int p, int t, Acc& acc) {
-    RowSel rs{kp.pp.mask, kp.pp.prefix};
+    RowSel rs{acc.smask, acc.spref, acc.wbase};
     int iy;
     const bool on = rs.get(t, iy);
     const float yv = on ? __ldg(kp.pp.ys + iy) : 0.f;

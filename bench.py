@@ -13,6 +13,13 @@ write) between steps, outside the timed events.  Plan construction (FP64
 spectrum, tables) and the power iteration are set-up, reported separately.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--iters T] [--impl reference]
+  python bench.py --workload batched [--steps K] [--warmup W] [--iters T]
+
+The batched workload: 512 independent instances, n log-uniform in
+[2^12, 2^20] (snapped to powers of two), m/n uniform in [0.2, 0.5], k/n =
+0.01, each with its own c; one step = T ISTA + T ADMM iterations of every
+instance through cs_batch_*, against the same work done by looping the plain
+per-instance solver (cs_ista / cs_admm on one plan per instance).
 
 Under torchrun each rank solves its own instance (replicas, no collective on
 the data path) and rank 0 prints one JSON line.
@@ -51,6 +58,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=1 << 22)
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-NMSE, roofline and CPU legs")
+    ap.add_argument("--workload", default="n2e22", choices=["n2e22", "batched"])
+    ap.add_argument("--batch", type=int, default=512, help="instances of the batched workload")
     return ap.parse_args()
 
 
@@ -411,10 +420,124 @@ def time_to_nmse(cs, plan, y, xt, tau, n, dev, torch):
     return res
 
 
+def run_batched(args):
+    """Batched solves against looping the plain solver (see the module
+    docstring); 1 GPU, device-timed with CUDA events, L2 flushed between
+    steps."""
+    # the batch's side streams need their own hardware queues (set before
+    # the CUDA context exists)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    import torch
+    import paper_1707_02244_gb300 as cs
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    T = args.iters
+    n, m = synth.batch_sizes(args.batch, 12, 20, synth.BATCH_SEED)
+    insts = synth.batch_instances(n, m)
+    noff = np.concatenate([[0], np.cumsum(n)[:-1]])
+    moff = np.concatenate([[0], np.cumsum(m)[:-1]])
+    N, M = int(n.sum()), int(m.sum())
+    t0 = time.perf_counter()
+    plans = [cs.cs_plan(i.n, i.m, i.rows, i.c, stream) for i in insts]
+    plans_s = time.perf_counter() - t0
+    xt = torch.from_numpy(np.concatenate([i.x_true for i in insts]).astype(np.float32)).to(dev)
+    y = torch.empty(M, dtype=torch.float32, device=dev)
+    taus = np.empty(len(insts), dtype=np.float32)
+    for j, p in enumerate(plans):
+        cs.cs_forward(p, xt[noff[j]:noff[j] + n[j]], y[moff[j]:moff[j] + m[j]])
+        taus[j] = np.float32(1.0 / cs.cs_opnorm2(p, 30))
+    y += torch.from_numpy(np.concatenate([i.noise for i in insts]).astype(np.float32)).to(dev)
+    t0 = time.perf_counter()
+    batch = cs.cs_batch_plan(n, m, np.concatenate([i.rows for i in insts]), np.concatenate([i.c for i in insts]),
+                             stream)
+    batch_plan_s = time.perf_counter() - t0
+    lam = np.full(len(insts), LAM, dtype=np.float32)
+    rho = np.full(len(insts), RHO, dtype=np.float32)
+    xb = torch.zeros(N, dtype=torch.float32, device=dev)
+    zb = torch.zeros(N, dtype=torch.float32, device=dev)
+    xl = torch.zeros(N, dtype=torch.float32, device=dev)
+    zl = torch.zeros(N, dtype=torch.float32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def batched():
+        xb.zero_()
+        cs.cs_batch_ista(batch, y, lam, taus, T, xb)
+        cs.cs_batch_admm(batch, y, lam, rho, T, zb)
+
+    def looped():
+        xl.zero_()
+        for j, p in enumerate(plans):
+            sl, sm = slice(noff[j], noff[j] + n[j]), slice(moff[j], moff[j] + m[j])
+            cs.cs_ista(p, y[sm], LAM, float(taus[j]), T, xl[sl], stats=False)
+            cs.cs_admm(p, y[sm], LAM, RHO, T, zl[sl], stats=False)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    clocks = Clocks(0)
+    clocks.start()
+    ms_b = timed(batched, args.steps)
+    ms_l = timed(looped, max(3, args.steps // 5)) if not args.no_extras else float("nan")
+    clk = clocks.stop()
+    assert cs.cs_batch_status_sync(batch) == cs.CS_OK
+
+    def nmse_per_instance(v):
+        d = (v - xt).double() ** 2
+        t2 = xt.double() ** 2
+        idx = torch.repeat_interleave(torch.arange(len(insts), device=dev), torch.from_numpy(n).to(dev))
+        num = torch.zeros(len(insts), dtype=torch.float64, device=dev).index_add_(0, idx, d)
+        den = torch.zeros(len(insts), dtype=torch.float64, device=dev).index_add_(0, idx, t2)
+        return (num / den).cpu().numpy()
+
+    nb, nl = nmse_per_instance(zb), nmse_per_instance(zl)
+    classes = {int(k): int(v) for k, v in zip(*np.unique(n, return_counts=True))}
+    line = {
+        "metric": "batched ISTA+ADMM instance-iterations/s (512 uneven instances) vs looping the plain solver",
+        "value": len(insts) * 2 * T / (ms_b / 1e3), "unit": "instance-iter/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched: {len(insts)} instances, n log-uniform [2^12, 2^20] snapped to powers "
+                               "of two, m/n uniform [0.2, 0.5], k/n=0.01, noise 1e-3, own c each; "
+                               f"lambda={LAM}, tau=1/||A_i||^2 (GPU power iteration), rho={RHO}",
+                   "iters_per_solver_per_step": T, "sum_n": N, "sum_m": M, "size_classes": classes,
+                   "l2": "flushed (512 MiB write) between steps, outside the timed events"},
+        "element_iter_per_s": N * 2 * T / (ms_b / 1e3),
+        "looped": {"ms_per_step": ms_l, "value": len(insts) * 2 * T / (ms_l / 1e3),
+                   "element_iter_per_s": N * 2 * T / (ms_l / 1e3)},
+        "speedup_vs_looped": ms_l / ms_b,
+        "admm_nmse_vs_xtrue_after_T": {"batched_median": float(np.median(nb)), "batched_max": float(nb.max()),
+                                       "looped_median": float(np.median(nl)), "looped_max": float(nl.max())},
+        "plan_s": {"batch": batch_plan_s, "per_instance_plans": plans_s},
+        "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+    for p in plans:
+        p.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_gpu(args)
 
 

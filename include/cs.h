@@ -155,6 +155,50 @@ cs_status cs_admm_ex(cs_plan_t plan, const float* y, float lambda,
  * (pass_id, reps < 1, no earlier solve of that kind). */
 cs_status cs_profile_pass(cs_plan_t plan, int pass_id, int reps);
 
+/* ---------------------------------------------------------------------
+ * Batched solves (no counterpart in the paper; its recovery problem solved
+ * for many independent instances at once).  Instance i has its own n_i,
+ * m_i, rows and c.  Instances with n_i <= CS_BATCH_MAX_N are solved one CTA
+ * per instance, the iterate kept in shared memory for all iterations (one
+ * launch per power-of-two size class); larger instances by a per-instance
+ * plan.  The work runs on internal streams (32; the environment variable
+ * CS_BATCH_STREAMS, read by cs_batch_plan, sets 1..32) that fork from and
+ * join back into the batch's stream, so instances overlap on the GPU.  They
+ * only run side by side if the process has as many hardware queues: set
+ * CUDA_DEVICE_MAX_CONNECTIONS=32 before the CUDA context is created (the
+ * CUDA default, 8, serialises the streams beyond the eighth).
+ * --------------------------------------------------------------------- */
+#define CS_BATCH_MAX_N 8192
+typedef struct cs_batch_s* cs_batch_t;
+
+/*   count     number of instances (>= 1)
+ *   n, m      HOST int64[count]: n_i power of two, 64 <= n_i <= 2^22;
+ *             1 <= m_i <= n_i
+ *   rows      HOST int64[sum m_i]: instance i's rows, concatenated
+ *   c         HOST float64[sum n_i]: instance i's first row of C, concatenated
+ * Synchronises.  Errors as cs_plan. */
+cs_status cs_batch_plan(cs_batch_t* out, int count, const int64_t* n, const int64_t* m,
+                        const int64_t* rows, const double* c, void* stream);
+cs_status cs_batch_destroy(cs_batch_t batch);
+
+/* ISTA (Algorithm 1) on every instance for `iters` iterations.
+ *   y       DEVICE float[sum m_i], instance i's measurements concatenated
+ *   lambda, tau  HOST float[count]
+ *   x       DEVICE float[sum n_i]: in x(0), out x(T), concatenated
+ * Asynchronous. */
+cs_status cs_batch_ista(cs_batch_t batch, const float* y, const float* lambda,
+                        const float* tau, int iters, float* x);
+
+/* ADMM (Algorithm 3, sigma = rho, tau1 = tau2 = 1, zero start) on every
+ * instance; z DEVICE float[sum n_i] receives z(T).  rho HOST float[count].
+ * Asynchronous. */
+cs_status cs_batch_admm(cs_batch_t batch, const float* y, const float* lambda,
+                        const float* rho, int iters, float* z);
+
+/* Waits for the batch's work; returns CS_ERR_NONFINITE if a measurement was
+ * not finite, else the first error latched by a per-instance plan. */
+cs_status cs_batch_status_sync(cs_batch_t batch);
+
 /* Largest n accepted by cs_circulant_apply_static. */
 #define CS_STATIC_MAX_N 16384
 

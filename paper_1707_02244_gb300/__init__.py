@@ -24,7 +24,8 @@ CS_OK, CS_ERR_ARG, CS_ERR_NOMEM, CS_ERR_CUDA, CS_ERR_TIMEOUT, CS_ERR_NONFINITE, 
 
 EXPORTS = ("cs_plan", "cs_plan_destroy", "cs_opnorm2", "cs_forward", "cs_adjoint",
            "cs_set_monitor", "cs_ista", "cs_admm", "cs_admm_ex", "cs_status_sync",
-           "cs_status_string", "cs_version", "cs_profile_pass", "cs_circulant_apply_static")
+           "cs_status_string", "cs_version", "cs_profile_pass", "cs_circulant_apply_static",
+           "cs_batch_plan", "cs_batch_destroy", "cs_batch_ista", "cs_batch_admm", "cs_batch_status_sync")
 
 
 class CsStats(ctypes.Structure):
@@ -68,6 +69,11 @@ def _load() -> ctypes.CDLL:
         "cs_status_sync": [vp],
         "cs_profile_pass": [vp, ci, ci],
         "cs_circulant_apply_static": [i64, vp, vp, vp, ci, vp],
+        "cs_batch_plan": [ctypes.POINTER(vp), ci, vp, vp, vp, vp, vp],
+        "cs_batch_destroy": [vp],
+        "cs_batch_ista": [vp, vp, vp, vp, ci, vp],
+        "cs_batch_admm": [vp, vp, vp, vp, ci, vp],
+        "cs_batch_status_sync": [vp],
         "cs_status_string": [ci],
         "cs_version": [],
     }
@@ -209,6 +215,72 @@ def cs_circulant_apply_static(n: int, c, x, y, transpose: bool = False, stream=N
     cptr = int(c.data_ptr()) if hasattr(c, "data_ptr") else int(c)
     _check(_lib.cs_circulant_apply_static(int(n), cptr, _ptr(x), _ptr(y), int(bool(transpose)),
                                           _stream_handle(stream)), "cs_circulant_apply_static")
+
+
+class BatchPlan:
+    """Owns a cs_batch_t: instances i = 0..count-1 with sizes n[i], m[i];
+    their vectors are concatenated in instance order (offsets noff / moff)."""
+
+    def __init__(self, handle: int, n, m):
+        self.handle = handle
+        self.n = np.asarray(n, dtype=np.int64)
+        self.m = np.asarray(m, dtype=np.int64)
+        self.noff = np.concatenate([[0], np.cumsum(self.n)[:-1]]).astype(np.int64)
+        self.moff = np.concatenate([[0], np.cumsum(self.m)[:-1]]).astype(np.int64)
+        self.count = len(self.n)
+
+    def close(self):
+        if self.handle:
+            _lib.cs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cs_batch_plan(n, m, rows, c, stream=None) -> BatchPlan:
+    """n, m: per-instance sizes; rows (int64) and c (float64): the instances'
+    rows and generating vectors, concatenated."""
+    n = np.ascontiguousarray(n, dtype=np.int64)
+    m = np.ascontiguousarray(m, dtype=np.int64)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    if n.shape != m.shape or rows.shape != (int(m.sum()),) or c.shape != (int(n.sum()),):
+        raise ValueError("rows must hold sum(m) entries and c sum(n)")
+    h = ctypes.c_void_p()
+    code = _lib.cs_batch_plan(ctypes.byref(h), len(n), n.ctypes.data, m.ctypes.data, rows.ctypes.data,
+                              c.ctypes.data, _stream_handle(stream))
+    _check(code, "cs_batch_plan")
+    return BatchPlan(h.value, n, m)
+
+
+def cs_batch_destroy(batch: BatchPlan):
+    batch.close()
+
+
+def _host_f32(v, count: int) -> np.ndarray:
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float32), (count,)))
+    return a
+
+
+def cs_batch_ista(batch: BatchPlan, y, lam, tau, iters: int, x):
+    """lam, tau: scalars or per-instance sequences (host)."""
+    lam_h, tau_h = _host_f32(lam, batch.count), _host_f32(tau, batch.count)
+    _check(_lib.cs_batch_ista(batch.handle, _ptr(y), lam_h.ctypes.data, tau_h.ctypes.data, int(iters), _ptr(x)),
+           "cs_batch_ista")
+
+
+def cs_batch_admm(batch: BatchPlan, y, lam, rho, iters: int, z):
+    lam_h, rho_h = _host_f32(lam, batch.count), _host_f32(rho, batch.count)
+    _check(_lib.cs_batch_admm(batch.handle, _ptr(y), lam_h.ctypes.data, rho_h.ctypes.data, int(iters), _ptr(z)),
+           "cs_batch_admm")
+
+
+def cs_batch_status_sync(batch: BatchPlan) -> int:
+    return int(_lib.cs_batch_status_sync(batch.handle))
 
 
 def cs_status_sync(plan: Plan) -> int:

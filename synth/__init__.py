@@ -92,6 +92,27 @@ def large_instance(seed: int = LARGE_SEED, n: int = 1 << 22) -> Instance:
     return instance(n, n // 4, p=1.0 / 200.0, noise_std=1e-4, seed=seed)
 
 
+BATCH_SEED = 1707003
+
+
+def batch_sizes(count: int, lg_lo: float, lg_hi: float, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """Sizes of a batch of independent instances: n log-uniform in
+    [2^lg_lo, 2^lg_hi], snapped to the nearest power of two (log2 rounded),
+    m/n uniform in [0.2, 0.5]."""
+    g = rng(seed)
+    lg = np.rint(g.uniform(lg_lo, lg_hi, size=count)).astype(np.int64)
+    n = np.left_shift(np.int64(1), lg)
+    m = np.maximum(1, np.rint(g.uniform(0.2, 0.5, size=count) * n)).astype(np.int64)
+    return n, m
+
+
+def batch_instances(n, m, *, k_frac: float = 0.01, noise_std: float = 1e-3, seed: int = BATCH_SEED) -> list:
+    """One instance per (n_i, m_i), each with its own c, rows and
+    max(1, k_frac * n_i)-sparse x*; instance i is seeded with seed + i."""
+    return [instance(int(ni), int(mi), k=max(1, int(round(k_frac * ni))), noise_std=noise_std, seed=seed + i)
+            for i, (ni, mi) in enumerate(zip(n, m))]
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     """Dense N(0,1) vector (operator tests)."""
     return rng(seed).standard_normal(n)

@@ -79,3 +79,31 @@ def test_null_plan_is_an_argument_error(cs):
     L = ctypes.c_double()
     assert cs.raw_call("cs_opnorm2", None, 10, ctypes.byref(L)) == cs.CS_ERR_ARG
     assert cs.raw_call("cs_set_monitor", None, None, ctypes.c_double(0.0), 10) == cs.CS_ERR_ARG
+
+
+def test_batch_plan_rejects_bad_arguments_without_device(cs):
+    h = ctypes.c_void_p()
+    n = np.array([64, 128], dtype=np.int64)
+    m = np.array([8, 16], dtype=np.int64)
+    rows = np.zeros(24, dtype=np.int64)
+    c = np.zeros(192)
+    args = [n.ctypes.data, m.ctypes.data, rows.ctypes.data, c.ctypes.data, None]
+    assert cs.raw_call("cs_batch_plan", None, 2, *args) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_batch_plan", ctypes.byref(h), 0, *args) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_batch_plan", ctypes.byref(h), 2, n.ctypes.data, m.ctypes.data, None,
+                       c.ctypes.data, None) == cs.CS_ERR_ARG
+    bad_m = np.array([8, 129], dtype=np.int64)
+    assert cs.raw_call("cs_batch_plan", ctypes.byref(h), 2, n.ctypes.data, bad_m.ctypes.data,
+                       rows.ctypes.data, c.ctypes.data, None) == cs.CS_ERR_ARG
+    for bad in (96, 32, 1 << 23):
+        bn = np.array([64, bad], dtype=np.int64)
+        assert cs.raw_call("cs_batch_plan", ctypes.byref(h), 2, bn.ctypes.data, m.ctypes.data,
+                           rows.ctypes.data, c.ctypes.data, None) == cs.CS_ERR_UNSUPPORTED, bad
+
+
+def test_null_batch_is_an_argument_error(cs):
+    lam = np.ones(2, dtype=np.float32)
+    assert cs.raw_call("cs_batch_destroy", None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_batch_ista", None, None, lam.ctypes.data, lam.ctypes.data, 1, None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_batch_admm", None, None, lam.ctypes.data, lam.ctypes.data, 1, None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_batch_status_sync", None) == cs.CS_ERR_ARG

@@ -40,6 +40,7 @@ __all__ = [
     "ista_fft", "admm_dense", "admm_fft", "admm_standard_dense",
     "admm_d_diagonal", "opnorm2_dense", "opnorm2_power_fft",
     "lasso_bruteforce", "l0_bruteforce", "nmse", "naive_dft",
+    "ista_unrolled_grad_dense", "ista_unrolled_grad_fft", "ista_unrolled_loss",
 ]
 
 
@@ -408,3 +409,85 @@ def l0_bruteforce(A, y, kmax, tol=1e-9):
         if fits:
             return xbest, fits
     return None, []
+
+
+# --------------------------------------------------------------------------
+# Reverse mode of unrolled ISTA (no counterpart in the paper: the derivative of
+# T steps of Algorithm 1, from x(0) = 0, with respect to c, lambda and y)
+# --------------------------------------------------------------------------
+#
+# One step is u = x + tau C^T M (P^T y - C x), x' = eta_theta(u), theta =
+# tau * lam (Eq. 4 with the threshold reading of Algorithm 1).  Given g =
+# dL/dx', the step's contributions are, with w = g on {|u| > theta} and 0
+# elsewhere (the soft threshold's derivative; |u| == theta counts as 0):
+#   dL/dx      = w - tau C^T M C w
+#   dL/dtheta += -sum(sign(u) w)            (dL/dlam = tau dL/dtheta)
+#   dL/dy     += tau P C w
+#   dL/dc_k   += tau (sum_i r_i w_{i+k} - sum_i q_i x_{i+k}),
+#                r = M (P^T y - C x),  q = M C w  (indices mod n),
+# the last from dC/dc_k = Pi_k, (Pi_k)_{ij} = 1 if (j - i) mod n == k, so that
+# w^T du/dc_k = tau ((Pi_k w)^T r - (M C w)^T (Pi_k x)).
+
+def _ista_grad(C_apply, Ct_apply, corr, n, rows, y, lam, tau, T, gx_T):
+    rows = np.asarray(rows, dtype=np.int64)
+    y = np.asarray(y, dtype=np.float64)
+    theta = tau * lam
+    mask = np.zeros(n)
+    mask[rows] = 1.0
+    pty = zero_fill(n, rows, y)
+    xs = [np.zeros(n)]
+    us = []
+    for _ in range(T):
+        x = xs[-1]
+        u = x + tau * Ct_apply(mask * (pty - C_apply(x)))
+        us.append(u)
+        xs.append(soft_threshold(u, theta))
+    g = np.asarray(gx_T, dtype=np.float64).copy()
+    dc = np.zeros(n)
+    dtheta = 0.0
+    dy = np.zeros(len(rows))
+    for t in range(T - 1, -1, -1):
+        x, u = xs[t], us[t]
+        w = np.where(np.abs(u) > theta, g, 0.0)
+        dtheta -= float(np.sum(np.sign(u) * w))
+        cw = C_apply(w)
+        q = mask * cw
+        dy += tau * cw[rows]
+        r = mask * (pty - C_apply(x))
+        dc += tau * (corr(r, w) - corr(q, x))
+        g = w - tau * Ct_apply(q)
+    return {"x_T": xs[-1], "dc": dc, "dlam": tau * dtheta, "dy": dy, "dx0": g}
+
+
+def ista_unrolled_grad_dense(c, rows, y, lam, tau, T, gx_T):
+    """Gradient of L(x(T)) for T ISTA steps from x(0) = 0 with respect to c,
+    lam and y, given gx_T = dL/dx(T).  Dense C; the correlation
+    sum_i b_i a_{(i+k) mod n} is formed for every k by rolling a."""
+    C = circulant_matrix(c)
+    n = C.shape[0]
+
+    def corr(b, a):
+        return np.array([np.dot(b, np.roll(a, -k)) for k in range(n)])
+
+    return _ista_grad(lambda v: C @ v, lambda v: C.T @ v, corr, n, rows, y, lam, tau, T, gx_T)
+
+
+def ista_unrolled_grad_fft(c, rows, y, lam, tau, T, gx_T):
+    """As ista_unrolled_grad_dense with the products and correlations taken
+    by FFT: DFT(sum_i b_i a_{i+k}) = conj(DFT b) DFT a for real a, b."""
+    chat = spectrum(c)
+    n = chat.shape[0]
+
+    def corr(b, a):
+        return np.fft.irfft(np.conj(np.fft.rfft(b)) * np.fft.rfft(a), n)
+
+    return _ista_grad(lambda v: circulant_apply_fft(chat, v), lambda v: circulant_apply_fft(chat, v, True),
+                      corr, n, rows, y, lam, tau, T, gx_T)
+
+
+def ista_unrolled_loss(c, rows, y, lam, tau, T, x_star, dense=True):
+    """L = ||x(T) - x*||^2 after T ISTA steps from x(0) = 0, and dL/dx(T)."""
+    run = ista_dense if dense else ista_fft
+    xT = run(c, rows, y, lam, tau, T)
+    d = xT - np.asarray(x_star, dtype=np.float64)
+    return float(np.dot(d, d)), 2.0 * d

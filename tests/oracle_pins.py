@@ -304,6 +304,77 @@ def check_opnorm(O):
     assert abs(L2 - sv) <= 1e-6 * sv
 
 
+# ---------------------------------------------------------------- unrolled ISTA gradient
+
+def _smooth_grad_instance(O, n, m, k, T, seed0, margin=1e-4):
+    """A seeded instance whose T ISTA iterates keep every |u| at least
+    `margin` away from the threshold (so that central differences with a
+    much smaller step never cross a kink of the soft threshold)."""
+    for seed in range(seed0, seed0 + 50):
+        inst = synth.instance(n, m, k=k, noise_std=1e-2, seed=seed)
+        A = O.sensing_matrix(inst.c, inst.rows)
+        y = A @ inst.x_true + inst.noise
+        tau = 0.9 / O.opnorm2_dense(inst.c, inst.rows)
+        lam = 0.05 * float(np.max(np.abs(A.T @ y)))
+        x = np.zeros(n)
+        gap = np.inf
+        for _ in range(T):
+            u = x + tau * (A.T @ (y - A @ x))
+            gap = min(gap, float(np.min(np.abs(np.abs(u) - tau * lam))))
+            x = O.soft_threshold(u, tau * lam)
+        if gap > margin and np.count_nonzero(x) > 0:
+            return inst, y, lam, tau
+    raise AssertionError("no smooth instance found")
+
+
+def check_unrolled_grad_finite_differences(O):
+    """The reverse-mode gradient of L = ||x(T) - x*||^2 (T ISTA steps from
+    x(0) = 0) equals central finite differences of the forward iteration
+    (ista_dense, itself pinned above) along random directions in c, y and
+    for lambda."""
+    n, m, T = 32, 14, 15
+    inst, y, lam, tau = _smooth_grad_instance(O, n, m, 3, T, 131)
+    L0, gx = O.ista_unrolled_loss(inst.c, inst.rows, y, lam, tau, T, inst.x_true)
+    gr = O.ista_unrolled_grad_dense(inst.c, inst.rows, y, lam, tau, T, gx)
+    h = 1e-6
+    g = synth.rng(132)
+
+    def loss(c, yy, ll):
+        return O.ista_unrolled_loss(c, inst.rows, yy, ll, tau, T, inst.x_true)[0]
+
+    dcdir = g.standard_normal(n)
+    fd = (loss(inst.c + h * dcdir, y, lam) - loss(inst.c - h * dcdir, y, lam)) / (2 * h)
+    an = float(np.dot(gr["dc"], dcdir))
+    assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), ("dc", fd, an)
+    dydir = g.standard_normal(m)
+    fd = (loss(inst.c, y + h * dydir, lam) - loss(inst.c, y - h * dydir, lam)) / (2 * h)
+    an = float(np.dot(gr["dy"], dydir))
+    assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), ("dy", fd, an)
+    fd = (loss(inst.c, y, lam + h) - loss(inst.c, y, lam - h)) / (2 * h)
+    assert abs(fd - gr["dlam"]) <= 1e-6 * max(1.0, abs(fd)), ("dlam", fd, gr["dlam"])
+    assert np.allclose(gr["x_T"], O.ista_dense(inst.c, inst.rows, y, lam, tau, T), atol=1e-14)
+
+
+def check_unrolled_grad_dense_fft_agree(O):
+    """Dense and FFT forms of the gradient agree to rounding, and the FFT
+    form also matches central differences at a larger size."""
+    n, m, T = 128, 50, 12
+    inst, y, lam, tau = _smooth_grad_instance(O, n, m, 5, T, 141)
+    _, gx = O.ista_unrolled_loss(inst.c, inst.rows, y, lam, tau, T, inst.x_true)
+    gd = O.ista_unrolled_grad_dense(inst.c, inst.rows, y, lam, tau, T, gx)
+    gf = O.ista_unrolled_grad_fft(inst.c, inst.rows, y, lam, tau, T, gx)
+    for key in ("dc", "dy", "dx0", "x_T"):
+        scale = max(1.0, float(np.max(np.abs(gd[key]))))
+        assert np.max(np.abs(gd[key] - gf[key])) <= 1e-10 * scale, key
+    assert abs(gd["dlam"] - gf["dlam"]) <= 1e-10 * max(1.0, abs(gd["dlam"]))
+    h = 1e-6
+    d = synth.rng(142).standard_normal(n)
+    lp = O.ista_unrolled_loss(inst.c + h * d, inst.rows, y, lam, tau, T, inst.x_true, dense=False)[0]
+    lm = O.ista_unrolled_loss(inst.c - h * d, inst.rows, y, lam, tau, T, inst.x_true, dense=False)[0]
+    fd = (lp - lm) / (2 * h)
+    assert abs(fd - float(np.dot(gf["dc"], d))) <= 1e-6 * max(1.0, abs(fd))
+
+
 ALL_CHECKS = [
     check_circulant_worked_example, check_eigenvalues_are_dft,
     check_fft_products_match_dense, check_adjoint_identity,
@@ -312,5 +383,5 @@ ALL_CHECKS = [
     check_ista_monotone, check_kkt_at_convergence,
     check_admm_fixed_point_relations, check_bruteforce_lasso,
     check_exact_recovery_tiny, check_admm_inverse, check_dense_fft_agree,
-    check_opnorm,
+    check_opnorm, check_unrolled_grad_finite_differences, check_unrolled_grad_dense_fft_agree,
 ]

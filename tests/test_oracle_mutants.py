@@ -90,6 +90,42 @@ def _admm_variant(drop_sigma=False, no_fold=False, nu_sign=+1, z_thr_rho=False):
     return _admm
 
 
+def _grad_variant(drop_q=False, active_from_x=False, dy_no_tau=False, dlam_sign=-1.0, corr_swap=False):
+    """_ista_grad with one planted mistake."""
+    def _g(C_apply, Ct_apply, corr, n, rows, y, lam, tau, T, gx_T):
+        rows = np.asarray(rows, dtype=np.int64)
+        y = np.asarray(y, dtype=np.float64)
+        theta = tau * lam
+        mask = np.zeros(n)
+        mask[rows] = 1.0
+        pty = O.zero_fill(n, rows, y)
+        xs = [np.zeros(n)]
+        us = []
+        for _ in range(T):
+            x = xs[-1]
+            u = x + tau * Ct_apply(mask * (pty - C_apply(x)))
+            us.append(u)
+            xs.append(O.soft_threshold(u, theta))
+        g = np.asarray(gx_T, dtype=np.float64).copy()
+        dc = np.zeros(n)
+        dtheta = 0.0
+        dy = np.zeros(len(rows))
+        for t in range(T - 1, -1, -1):
+            x, u = xs[t], us[t]
+            act = (np.abs(x) > 0) if active_from_x else (np.abs(u) > theta)
+            w = np.where(act, g, 0.0)
+            dtheta += dlam_sign * float(np.sum(np.sign(u) * w))
+            cw = C_apply(w)
+            q = mask * cw
+            dy += (1.0 if dy_no_tau else tau) * cw[rows]
+            r = mask * (pty - C_apply(x))
+            term = corr(w, r) if corr_swap else corr(r, w)
+            dc += tau * (term - (0.0 if drop_q else corr(q, x)))
+            g = w - tau * Ct_apply(q)
+        return {"x_T": xs[-1], "dc": dc, "dlam": tau * dtheta, "dy": dy, "dx0": g}
+    return _g
+
+
 MUTANTS = {
     "transposed_circulant": ("circulant_matrix", _mut_transposed_circulant),
     "reverse_circulant": ("circulant_matrix", _mut_reverse_circulant),
@@ -102,6 +138,11 @@ MUTANTS = {
     "admm_no_fold": ("_admm", _admm_variant(no_fold=True)),
     "admm_nu_sign": ("_admm", _admm_variant(nu_sign=-1)),
     "admm_threshold_rho": ("_admm", _admm_variant(z_thr_rho=True)),
+    "grad_drop_q_term": ("_ista_grad", _grad_variant(drop_q=True)),
+    "grad_active_from_x": ("_ista_grad", _grad_variant(active_from_x=True)),
+    "grad_dy_no_tau": ("_ista_grad", _grad_variant(dy_no_tau=True)),
+    "grad_dlam_sign": ("_ista_grad", _grad_variant(dlam_sign=+1.0)),
+    "grad_corr_swapped": ("_ista_grad", _grad_variant(corr_swap=True)),
 }
 
 

@@ -14,6 +14,7 @@ spectrum, tables) and the power iteration are set-up, reported separately.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--iters T] [--impl reference]
   python bench.py --workload batched [--steps K] [--warmup W] [--iters T]
+  python bench.py --workload grad [--steps K] [--warmup W]
 
 The batched workload: 512 independent instances, n log-uniform in
 [2^12, 2^20] (snapped to powers of two), m/n uniform in [0.2, 0.5], k/n =
@@ -58,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=1 << 22)
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-NMSE, roofline and CPU legs")
-    ap.add_argument("--workload", default="n2e22", choices=["n2e22", "batched"])
+    ap.add_argument("--workload", default="n2e22", choices=["n2e22", "batched", "grad"])
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched workload")
     return ap.parse_args()
 
@@ -532,12 +533,87 @@ def run_batched(args):
     return 0
 
 
+def run_grad(args):
+    """Differentiable form: unrolled ISTA T = 300 on n = 2^20, m = n/4 (k =
+    n/100, noise 1e-3, lambda = 5e-3, tau = 0.9/||C||^2 by power iteration),
+    loss ||x(T) - x*||^2; one step = cs_grad (forward with checkpoints every
+    25 steps, replay, reverse) against the plain solve cs_ista(T) on the same
+    plan.  Device-timed, L2 flushed between steps."""
+    import torch
+    import paper_1707_02244_gb300 as cs
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    n, T, K = 1 << 20, 300, 25
+    inst = synth.instance(n, n // 4, k=n // 100, noise_std=1e-3, seed=8300)
+    m = inst.m
+    plan = cs.cs_plan(n, m, inst.rows, inst.c, stream)
+    xt = torch.from_numpy(inst.x_true.astype(np.float32)).to(dev)
+    y = torch.empty(m, dtype=torch.float32, device=dev)
+    cs.cs_forward(plan, xt, y)
+    y += torch.from_numpy(inst.noise.astype(np.float32)).to(dev)
+    tau = float(np.float32(0.9 / cs.cs_opnorm2(plan, 100)))
+    x = torch.zeros(n, dtype=torch.float32, device=dev)
+    dc = torch.empty(n, dtype=torch.float32, device=dev)
+    dl = torch.empty(1, dtype=torch.float32, device=dev)
+    dy = torch.empty(m, dtype=torch.float32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    cs.cs_ista(plan, y, LAM, tau, T, x, stats=False)
+    gx = 2.0 * (x - xt)
+
+    def solve():
+        x.zero_()
+        cs.cs_ista(plan, y, LAM, tau, T, x, stats=False)
+
+    def grad():
+        cs.cs_grad(plan, y, LAM, tau, T, K, gx, dc, dl, dy)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    clocks = Clocks(0)
+    clocks.start()
+    ms_g = timed(grad)
+    ms_s = timed(solve)
+    clk = clocks.stop()
+    assert cs.cs_status_sync(plan) == cs.CS_OK
+    line = {
+        "metric": "unrolled-ISTA gradient (dL/dc, dL/dlambda, dL/dy) time vs the plain solve, n=2^20, T=300",
+        "value": ms_g, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "unrolled ISTA T=300, checkpoints every 25, n=2^20, m=n/4, k=n/100, noise 1e-3, "
+                               f"lambda={LAM}, tau=0.9/||A||^2, loss ||x_T - x*||^2",
+                   "l2": "flushed (512 MiB write) between steps, outside the timed events"},
+        "plain_solve_ms": ms_s, "grad_over_solve": ms_g / ms_s,
+        "grad_ms_per_unrolled_step": ms_g / T, "solve_ms_per_iter": ms_s / T,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "grad":
+        return run_grad(args)
     return run_gpu(args)
 
 

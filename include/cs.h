@@ -155,6 +155,25 @@ cs_status cs_admm_ex(cs_plan_t plan, const float* y, float lambda,
  * (pass_id, reps < 1, no earlier solve of that kind). */
 cs_status cs_profile_pass(cs_plan_t plan, int pass_id, int reps);
 
+/* Gradient of unrolled ISTA (no counterpart in the paper: reverse mode
+ * through T steps of Algorithm 1, for calibration of c, lambda or y by
+ * gradient descent).  With x(0) = 0 and x(t+1) = eta_{tau lambda}(x(t) +
+ * tau A^T (y - A x(t))) as cs_ista computes it, and gx_T = dL/dx(T) for any
+ * loss L(x(T)):
+ *   dc      DEVICE float[n]: dL/dc (c as given to cs_plan, natural order)
+ *   dlambda DEVICE float[1]: dL/dlambda
+ *   dy      DEVICE float[m]: dL/dy (y[i] pairs with rows[i] as given)
+ * tau is held fixed (it is not differentiated through ||A||^2).  The
+ * soft threshold's derivative is taken as 1 where |u| > tau lambda and 0
+ * elsewhere (its value at the kink is a convention).
+ * The forward iterates are kept every K steps (checkpoints, (T/K + 1) n
+ * floats) and each segment of K steps is replayed before it is
+ * back-propagated ((2K + 4) n more floats, allocated by the first call and
+ * kept by the plan).  1 <= K <= T.  Asynchronous; errors as cs_ista.
+ * Uses the plan's solver state: not concurrent with cs_ista / cs_admm. */
+cs_status cs_grad(cs_plan_t plan, const float* y, float lambda, float tau, int T, int K,
+                  const float* gx_T, float* dc, float* dlambda, float* dy);
+
 /* ---------------------------------------------------------------------
  * Batched solves (no counterpart in the paper; its recovery problem solved
  * for many independent instances at once).  Instance i has its own n_i,

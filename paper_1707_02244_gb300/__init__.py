@@ -25,7 +25,8 @@ CS_OK, CS_ERR_ARG, CS_ERR_NOMEM, CS_ERR_CUDA, CS_ERR_TIMEOUT, CS_ERR_NONFINITE, 
 EXPORTS = ("cs_plan", "cs_plan_destroy", "cs_opnorm2", "cs_forward", "cs_adjoint",
            "cs_set_monitor", "cs_ista", "cs_admm", "cs_admm_ex", "cs_status_sync",
            "cs_status_string", "cs_version", "cs_profile_pass", "cs_circulant_apply_static",
-           "cs_batch_plan", "cs_batch_destroy", "cs_batch_ista", "cs_batch_admm", "cs_batch_status_sync")
+           "cs_batch_plan", "cs_batch_destroy", "cs_batch_ista", "cs_batch_admm", "cs_batch_status_sync",
+           "cs_grad")
 
 
 class CsStats(ctypes.Structure):
@@ -69,6 +70,7 @@ def _load() -> ctypes.CDLL:
         "cs_status_sync": [vp],
         "cs_profile_pass": [vp, ci, ci],
         "cs_circulant_apply_static": [i64, vp, vp, vp, ci, vp],
+        "cs_grad": [vp, vp, f32, f32, ci, ci, vp, vp, vp, vp],
         "cs_batch_plan": [ctypes.POINTER(vp), ci, vp, vp, vp, vp, vp],
         "cs_batch_destroy": [vp],
         "cs_batch_ista": [vp, vp, vp, vp, ci, vp],
@@ -203,6 +205,63 @@ def cs_admm_ex(plan: Plan, y, lam: float, sigma: float, rho: float, tau1: float,
                            ctypes.byref(st) if stats else None)
     _check(code, "cs_admm_ex")
     return st.as_dict() if stats else None
+
+
+def cs_grad(plan: Plan, y, lam: float, tau: float, T: int, K: int, gx_T, dc, dlam, dy):
+    """Reverse mode of T ISTA steps from x(0) = 0: dc, dlam (1 element) and
+    dy receive dL/dc, dL/dlambda, dL/dy for gx_T = dL/dx(T)."""
+    _check(_lib.cs_grad(plan.handle, _ptr(y), lam, tau, int(T), int(K), _ptr(gx_T), _ptr(dc), _ptr(dlam),
+                        _ptr(dy)), "cs_grad")
+
+
+def _make_unrolled_ista():
+    import torch
+
+    class UnrolledISTA(torch.autograd.Function):
+        """x(T) of T ISTA steps from x(0) = 0, differentiable in c, y and lam.
+
+        apply(c, y, lam, rows, tau, T, K): c float64 (n,) tensor (any device;
+        a plan is made from it), y float32 CUDA (m,), lam a 0-d tensor or
+        float, rows int64 (m,) array; tau, T, K plain numbers.  Forward runs
+        cs_ista, backward cs_grad (checkpoints every K steps)."""
+
+        @staticmethod
+        def forward(ctx, c, y, lam, rows, tau, T, K):
+            lam_f = float(lam)
+            n, m = int(c.shape[0]), int(y.shape[0])
+            stream = torch.cuda.current_stream(y.device)
+            plan = cs_plan(n, m, np.asarray(rows), c.detach().double().cpu().numpy(), stream)
+            x = torch.zeros(n, dtype=torch.float32, device=y.device)
+            cs_ista(plan, y.detach().contiguous(), lam_f, float(tau), int(T), x, stats=False)
+            ctx.plan, ctx.args = plan, (lam_f, float(tau), int(T), int(K))
+            ctx.c_meta = (c.dtype, c.device)
+            ctx.lam_is_tensor = torch.is_tensor(lam)
+            ctx.save_for_backward(y)
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            (y,) = ctx.saved_tensors
+            lam_f, tau, T, K = ctx.args
+            dc = torch.empty(ctx.plan.n, dtype=torch.float32, device=y.device)
+            dl = torch.empty(1, dtype=torch.float32, device=y.device)
+            dy = torch.empty(ctx.plan.m, dtype=torch.float32, device=y.device)
+            cs_grad(ctx.plan, y.detach().contiguous(), lam_f, tau, T, K, gx.contiguous().float(), dc, dl, dy)
+            code = cs_status_sync(ctx.plan)
+            ctx.plan.close()
+            _check(code, "cs_grad")
+            dlam = dl.reshape(()) if ctx.lam_is_tensor else None
+            return dc.to(dtype=ctx.c_meta[0], device=ctx.c_meta[1]), dy, dlam, None, None, None, None
+
+    return UnrolledISTA
+
+
+def __getattr__(name):
+    if name == "UnrolledISTA":
+        cls = _make_unrolled_ista()
+        globals()["UnrolledISTA"] = cls
+        return cls
+    raise AttributeError(name)
 
 
 def cs_profile_pass(plan: Plan, pass_id: int, reps: int = 1):

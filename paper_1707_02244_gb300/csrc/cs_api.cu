@@ -62,6 +62,19 @@ struct cs_plan_s {
   std::map<uint64_t, int> graph_nodes;
   std::map<uint64_t, cudaGraphExec_t> graphs;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // unrolled-ISTA gradient (cs_grad): allocated at the first call, grown on demand
+  struct Grad {
+    int ck_cap = 0, seg_cap = 0;
+    float* ckpt = nullptr;   // [ck_cap][n]  x(sK), tile order
+    float* seg = nullptr;    // [seg_cap + 1][n]  x(t) of the segment being replayed
+    float* rseg = nullptr;   // [seg_cap][n]  r(t) of the segment
+    float *g = nullptr, *w = nullptr, *q = nullptr;
+    float* dy = nullptr;     // [m] dL/dy, compact in the tile order of the rows
+    float2* W2 = nullptr;
+    float4* gacc = nullptr;  // spectrum of dL/dc (before tau), per pair slot
+    double* gpart = nullptr; // per column CTA: dL/dtheta
+    CallArgs* ca = nullptr;  // [seg_cap + 1]: step j of a segment, and the output pass
+  } gr;
 };
 
 namespace {
@@ -129,6 +142,10 @@ void free_plan(cs_plan_s* p) {
                   p->dense, p->dense2, p->dense3};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  void* gbufs[] = {p->gr.ckpt, p->gr.seg, p->gr.rseg, p->gr.g, p->gr.w, p->gr.q, p->gr.dy, p->gr.W2, p->gr.gacc,
+                   p->gr.gpart, p->gr.ca};
+  for (void* b : gbufs)
+    if (b) cudaFree(b);
   if (p->host_stats) cudaFreeHost(p->host_stats);
   if (p->host_status) cudaFreeHost(p->host_status);
   if (p->cap) cudaStreamDestroy(p->cap);
@@ -152,6 +169,9 @@ KParams kparams(const cs_plan_s* p, const Geo& g, int flags) {
   k.pp.tab_admm_c = p->tab_admm_c;
   k.pp.tab_admm_b = p->tab_admm_b;
   k.pp.status = p->status;
+  k.pp.W2 = p->gr.W2;
+  k.pp.gacc = p->gr.gacc;
+  k.pp.gpart = p->gr.gpart;
   k.ca = p->ca;
   k.flags = flags;
   return k;
@@ -695,6 +715,188 @@ cs_status cs_admm(cs_plan_t p, const float* y, float lambda, float rho, int iter
   cs_admm_params prm{rho, rho, 1.0, 1.0};
   // zero start; only z is returned
   return admm_impl(p, y, lambda, &prm, iters, 0, nullptr, z, nullptr, nullptr, nullptr, stats);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ gradient
+
+namespace {
+
+// (Re)allocate the gradient buffers for ck checkpoints and segments of up to
+// seg steps; cached graphs of the gradient (which hold the old addresses)
+// are dropped.
+cudaError_t grad_reserve(cs_plan_s* p, int ck, int seg) {
+  auto& G = p->gr;
+  if (G.ckpt && ck <= G.ck_cap && seg <= G.seg_cap) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return e;
+  for (auto it = p->graphs.begin(); it != p->graphs.end();) {
+    if ((it->first >> 40) >= 3) {
+      cudaGraphExecDestroy(it->second);
+      it = p->graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  const int nck = ck > G.ck_cap ? ck : G.ck_cap, nseg = seg > G.seg_cap ? seg : G.seg_cap;
+  void* old[] = {G.ckpt, G.seg, G.rseg, G.g, G.w, G.q, G.dy, G.W2, G.gacc, G.gpart, G.ca};
+  for (void* b : old)
+    if (b) cudaFree(b);
+  G = cs_plan_s::Grad{};
+  const size_t n = (size_t)p->n;
+  e = dalloc(&G.ckpt, (size_t)nck * n);
+  if (e == cudaSuccess) e = dalloc(&G.seg, (size_t)(nseg + 1) * n);
+  if (e == cudaSuccess) e = dalloc(&G.rseg, (size_t)nseg * n);
+  if (e == cudaSuccess) e = dalloc(&G.g, n);
+  if (e == cudaSuccess) e = dalloc(&G.w, n);
+  if (e == cudaSuccess) e = dalloc(&G.q, n);
+  if (e == cudaSuccess) e = dalloc(&G.dy, (size_t)p->m);
+  if (e == cudaSuccess) e = dalloc(&G.W2, n / 2);
+  if (e == cudaSuccess) e = dalloc(&G.gacc, (size_t)tab_count(p->gi));
+  if (e == cudaSuccess) e = dalloc(&G.gpart, (size_t)p->gi.col_ctas);
+  if (e == cudaSuccess) e = dalloc(&G.ca, (size_t)nseg + 1);
+  if (e == cudaSuccess) {
+    G.ck_cap = nck;
+    G.seg_cap = nseg;
+  }
+  return e;
+}
+
+// Run `enqueue` on the plan's stream, as a cached CUDA graph under `key`.
+template <class F>
+cudaError_t run_graph(cs_plan_s* p, uint64_t key, F&& enqueue) {
+  if (!p->use_graphs) return enqueue(p->stream);
+  auto it = p->graphs.find(key);
+  if (it == p->graphs.end()) {
+    cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t e2 = enqueue(p->cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(p->cap, &graph);
+    if (e2 != cudaSuccess || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return e2 != cudaSuccess ? e2 : e;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    it = p->graphs.emplace(key, exec).first;
+  }
+  return cudaGraphLaunch(it->second, p->stream);
+}
+
+KParams kp_step(const cs_plan_s* p, int j, int flags) {
+  KParams k = kparams(p, p->gi, flags);
+  k.ca = p->gr.ca + j;
+  return k;
+}
+
+// Replay of one segment: x(0) of the segment in seg[0]; step j writes r(j)
+// and x(j+1).
+cudaError_t enqueue_replay(cs_plan_s* p, int L, cudaStream_t s) {
+  const Geo& g = p->gi;
+  cudaError_t e = launch_col(COL_LOADT, kp_step(p, 0, 0), s);
+  for (int j = 0; j < L && e == cudaSuccess; ++j) {
+    e = launch_mid(MID_FWD, kp_step(p, j, 0), s);
+    if (e == cudaSuccess) e = launch_col(COL_RES_SAVE, kp_step(p, j, 0), s);
+    if (e == cudaSuccess) e = launch_mid(MID_ADJ, kp_step(p, j, 0), s);
+    if (e == cudaSuccess) e = launch_col(COL_ISTA_SEG, kp_step(p, j, 0), s);
+  }
+  (void)g;
+  return e;
+}
+
+// Reverse steps L-1 .. 0 of one segment (g holds dL/dx at its end).
+cudaError_t enqueue_reverse(cs_plan_s* p, int L, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (int j = L - 1; j >= 0 && e == cudaSuccess; --j) {
+    e = launch_col(COL_GRAD_W, kp_step(p, j, 0), s);
+    if (e == cudaSuccess) e = launch_mid(MID_FWD, kp_step(p, j, 0), s);
+    if (e == cudaSuccess) e = launch_col(COL_GRAD_MASK, kp_step(p, j, 0), s);
+    if (e == cudaSuccess) e = launch_mid(MID_ADJ, kp_step(p, j, 0), s);
+    if (e == cudaSuccess) e = launch_col(COL_GRAD_G, kp_step(p, j, 0), s);
+    if (e == cudaSuccess) e = launch_col(COL_LOAD2, kp_step(p, j, 0), s);
+    if (e == cudaSuccess) e = launch_mid(MID_CORR, kp_step(p, j, 0), s);
+    if (e == cudaSuccess) e = launch_col(COL_LOAD2, kp_step(p, j, FL_PAIR2), s);
+    if (e == cudaSuccess) e = launch_mid(MID_CORR, kp_step(p, j, FL_PAIR2), s);
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+cs_status cs_grad(cs_plan_t p, const float* y, float lambda, float tau, int T, int K, const float* gx_T,
+                  float* dc, float* dlambda, float* dy) {
+  if (!p || !y || !valid_ptr(gx_T) || !valid_ptr(dc) || !dlambda || !dy || T < 1 || K < 1 || K > T ||
+      !(lambda >= 0.f) || !(tau > 0.f) || !std::isfinite(lambda) || !std::isfinite(tau))
+    return CS_ERR_ARG;
+  cudaStream_t s = p->stream;
+  const int S = (T + K - 1) / K;   // segments; segment s covers steps [sK, min((s+1)K, T))
+  CS_TRY(grad_reserve(p, S, K));
+  auto& G = p->gr;
+  const size_t n = (size_t)p->n;
+  p->launches = 0;
+  const float thr = (float)((double)tau * (double)lambda);
+
+  // forward: T steps of Algorithm 1 from x(0) = 0, x(sK) kept
+  CallArgs a{};
+  a.x = p->xi_t;
+  a.thr = thr;
+  a.tau = tau;
+  CS_TRY(launch_set_args(a, p->ca, s));
+  CS_TRY(launch_scatter_y(y, p->si.pos, p->m, p->si.ys, p->status, s));
+  CS_TRY(cudaMemsetAsync(p->xi_t, 0, n * sizeof(float), s));
+  CS_TRY(cudaMemsetAsync(p->W, 0, n * sizeof(float), s));   // FFT of x(0) = 0
+  p->launches += 2;
+  for (int sg = 0; sg < S; ++sg) {
+    const int L = (sg + 1) * K <= T ? K : T - sg * K;
+    CS_TRY(cudaMemcpyAsync(G.ckpt + sg * n, p->xi_t, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CS_TRY(run_chunk(p, K_ISTA, L, sg == S - 1));
+  }
+  p->ista_args = false;
+  p->admm_args = false;
+
+  // per-step arguments of a segment
+  for (int j = 0; j <= K; ++j) {
+    CallArgs b{};
+    b.x = G.seg + j * n;
+    b.z = G.seg + (j + 1) * n;
+    b.v = G.rseg + j * n;
+    b.mu = G.w;
+    b.nu = G.q;
+    b.dst = j < K ? G.g : dc;   // entry K: the output pass (dL/dc, natural order)
+    b.aux = G.dy;
+    b.thr = thr;
+    b.tau = tau;
+    CS_TRY(launch_set_args(b, G.ca + j, s));
+  }
+  p->launches += K + 1;
+  CS_TRY(launch_to_tile(gx_T, G.g, p->gi, 1, s));
+  CS_TRY(cudaMemsetAsync(G.gacc, 0, tab_count(p->gi) * sizeof(float4), s));
+  CS_TRY(cudaMemsetAsync(G.gpart, 0, p->gi.col_ctas * sizeof(double), s));
+  CS_TRY(cudaMemsetAsync(G.dy, 0, p->m * sizeof(float), s));
+  p->launches += 1;
+
+  // reverse, segment by segment: replay from the checkpoint, then back-propagate
+  for (int sg = S - 1; sg >= 0; --sg) {
+    const int L = (sg + 1) * K <= T ? K : T - sg * K;
+    CS_TRY(cudaMemcpyAsync(G.seg, G.ckpt + sg * n, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CS_TRY(run_graph(p, (uint64_t(3) << 40) | (uint32_t)L, [&](cudaStream_t st) { return enqueue_replay(p, L, st); }));
+    CS_TRY(run_graph(p, (uint64_t(4) << 40) | (uint32_t)L, [&](cudaStream_t st) { return enqueue_reverse(p, L, st); }));
+    p->launches += 1 + 4 * L + 9 * L;
+  }
+
+  // outputs: dL/dc from its spectrum, dL/dlambda = tau dL/dtheta, dL/dy by row
+  CS_TRY(launch_mid(MID_FROM_ACC, kp_step(p, K, 0), s));
+  CS_TRY(launch_col(COL_STORE, kp_step(p, K, 0), s));
+  CS_TRY(launch_sum_scaled(G.gpart, p->gi.col_ctas, tau, dlambda, s));
+  CS_TRY(launch_gather_rows(G.dy, p->si.pos, p->m, dy, s));
+  p->launches += 4;
+  return CS_OK;
 }
 
 }  // extern "C"

@@ -221,6 +221,20 @@ __global__ void scatter_y_k(const float* __restrict__ y, const int32_t* __restri
   ys[pos[i]] = v;
 }
 
+__global__ void __launch_bounds__(AUX_NT) sum_scaled_k(const double* __restrict__ v, int count, float scale,
+                                                       float* __restrict__ out) {
+  __shared__ double red[AUX_NT];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < count; b += AUX_NT) s += v[b];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = AUX_NT / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = (float)((double)scale * red[0]);
+}
+
 __global__ void gather_rows_k(const float* __restrict__ dense, const int32_t* __restrict__ rows32, int64_t m,
                               float* __restrict__ y) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -379,6 +393,11 @@ cudaError_t launch_row_pos(const int64_t* rows, int64_t m, const Geo& g, int pac
 cudaError_t launch_scatter_y(const float* y, const int32_t* pos, int64_t m, float* ys, int* status,
                              cudaStream_t s) {
   scatter_y_k<<<blocks_for(m), AUX_NT, 0, s>>>(y, pos, m, ys, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_scaled(const double* v, int count, float scale, float* out, cudaStream_t s) {
+  sum_scaled_k<<<1, AUX_NT, 0, s>>>(v, count, scale, out);
   return cudaGetLastError();
 }
 

@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB) col_kernel(const KPa
     }
     __syncthreads();
   }
+  if constexpr (KIND == COL_GRAD_W) block_accum<NT>(acc.v[0], kp.pp.gpart);
   if (kp.flags & FL_STATS) {
     constexpr int kSlots =
         KIND == COL_RESIDUAL ? (1 << ST_R2)
@@ -145,6 +146,24 @@ __global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB) col_kernel(const KPa
       }
     }
   }
+  if constexpr (KIND == COL_LOAD2) {
+    // the second vector of the pair, to the second exchange buffer
+    __syncthreads();
+    for (int e = threadIdx.x; e < tot; e += NT) sm[pad(e)] = Epi<COL_LOAD2>::apply2(kp, a, (col0 << lgN2) + e);
+    __syncthreads();
+    tile_fft<-1, TILE, NT, TWS>(sm, lay, tw, lgN2);
+    float2* __restrict__ W2 = kp.pp.W2;
+#pragma unroll
+    for (int i = 0; i < NLD; ++i) {
+      const int e = 2 * (threadIdx.x + i * NT);
+      if (e < tot) {
+        const int j2 = e >> lgG, c = e & (G - 1);
+        const float2 lo = sm[pad(e)], hi = sm[pad(e + 1)];
+        __stcg(reinterpret_cast<float4*>(W2 + col0 + c + ((size_t)j2 << g.lgN1)),
+               make_float4(lo.x, lo.y, hi.x, hi.y));
+      }
+    }
+  }
 }
 
 }  // namespace
@@ -152,7 +171,8 @@ __global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB) col_kernel(const KPa
 #define CS_COL_KINDS(X, S)                                                                     \
   X(COL_LOAD, S) X(COL_LOAD_SCALED, S) X(COL_STORE, S) X(COL_MASK, S) X(COL_RESIDUAL, S)         \
   X(COL_ISTA, S) X(COL_ISTA_LAST, S) X(COL_POWER_OUT, S) X(COL_ADMM_INIT, S) X(COL_ADMM, S)       \
-  X(COL_ADMM_LAST, S)
+  X(COL_ADMM_LAST, S) X(COL_LOADT, S) X(COL_RES_SAVE, S) X(COL_ISTA_SEG, S) X(COL_GRAD_W, S)           \
+  X(COL_GRAD_MASK, S) X(COL_GRAD_G, S) X(COL_LOAD2, S)
 
 cudaError_t init_col_kernels() {
   cudaError_t e = cudaSuccess;

@@ -52,6 +52,10 @@ struct PlanPtrs {
   const float2* tab_admm_c;  // chat_k per pair slot, complex-n geometry
   const float* tab_admm_b;   // 1 / (n (rho |chat_k|^2 + sigma)) per pair slot
   int* status;               // device status word
+  // unrolled-ISTA gradient (cs_grad) only
+  float2* W2;                // second exchange buffer, complex[N] of the real-FFT geometry
+  float4* gacc;              // per pair slot: accumulated spectrum at (k, k + N)
+  double* gpart;             // per column CTA: accumulated dL/dtheta
 };
 
 // Per-call arguments, resident in device memory and written by a one-thread
@@ -79,7 +83,7 @@ struct KParams {
   int flags;
 };
 
-enum : int { FL_STATS = 1, FL_WRITE_STATE = 2, FL_POWER_SCALE = 4 };
+enum : int { FL_STATS = 1, FL_WRITE_STATE = 2, FL_POWER_SCALE = 4, FL_PAIR2 = 8 };
 
 // Column-pass epilogues and mid-pass spectrum operators.
 enum ColKind : int {
@@ -93,9 +97,21 @@ enum ColKind : int {
   COL_POWER_OUT,       // inverse, w -> dst, stats <u, w>, ||w||^2
   COL_ADMM_INIT,       // complex-n geometry: forward FFT of (v) + i (z - nu)
   COL_ADMM,            // inverse, Algorithm 3 elementwise steps, forward
-  COL_ADMM_LAST        // same without the forward FFT
+  COL_ADMM_LAST,       // same without the forward FFT
+  // unrolled-ISTA gradient (real-FFT geometry, vectors in tile order)
+  COL_LOADT,           // forward FFT of x (tile order)
+  COL_RES_SAVE,        // as COL_RESIDUAL, and r -> v
+  COL_ISTA_SEG,        // inverse, z <- eta(x + tau g) (x kept), forward
+  COL_GRAD_W,          // w = dst on the support of z -> mu, dtheta partials, forward
+  COL_GRAD_MASK,       // inverse, q = M C w -> nu, aux += tau P C w, forward
+  COL_GRAD_G,          // inverse, dst = mu - tau C^T q
+  COL_LOAD2            // forward FFTs of (v, mu) -> (W, W2); with FL_PAIR2 of (nu, x)
 };
-enum MidKind : int { MID_FWD = 0, MID_ADJ, MID_ADMM };
+enum MidKind : int {
+  MID_FWD = 0, MID_ADJ, MID_ADMM,
+  MID_CORR,            // forward FFTs of W and W2 -> gacc += s conj(a^) b^ (s = -1 with FL_PAIR2)
+  MID_FROM_ACC         // tau / N times the packed spectrum of gacc -> inverse FFT -> W
+};
 
 // Launchers (cs_passes.cu).  Return cudaGetLastError() of the launch.
 cudaError_t launch_col(ColKind kind, const KParams& kp, cudaStream_t s);
@@ -143,6 +159,8 @@ cudaError_t launch_scatter_rows(const float* r, const int32_t* rows32, int64_t m
 cudaError_t launch_norm2(const float* x, int64_t n, double* partials, double* out,
                          cudaStream_t s);
 cudaError_t launch_power_init(float* u, int64_t n, cudaStream_t s);
+// out[0] = scale * sum(v[0 .. count)), summed in a fixed order in FP64.
+cudaError_t launch_sum_scaled(const double* v, int count, float scale, float* out, cudaStream_t s);
 
 // Device status bits.
 enum : int { STS_NONFINITE = 1, STS_TIMEOUT = 2, STS_BAD_ROW = 4, STS_DUP_ROW = 8 };

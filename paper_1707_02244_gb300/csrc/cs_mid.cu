@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
   }
   pdl_wait();   // the twiddle tables above are plan constants; W is not
   const float a_rho = kp.ca->rho, a_sigma = kp.ca->sigma;   // ADMM only
-  {
+  auto load_tile = [&](float2* dst, const float2* __restrict__ src) {
     float4 buf[NLD];
 #pragma unroll
     for (int i = 0; i < NLD; ++i) {
@@ -189,36 +189,37 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
       if (e < tot) {
         const int slot = e >> lgN1, j1 = e & (N1 - 1);
         const int k2 = slot_row(g, u0 + (slot >> 1), slot & 1);
-        buf[i] = __ldcg(reinterpret_cast<const float4*>(W + ((size_t)k2 << lgN1) + j1));
+        buf[i] = __ldcg(reinterpret_cast<const float4*>(src + ((size_t)k2 << lgN1) + j1));
       }
     }
 #pragma unroll
     for (int i = 0; i < NLD; ++i) {
       const int e = 2 * (threadIdx.x + i * NT);
       if (e < tot) {
-        sm[pad(e)] = make_float2(buf[i].x, buf[i].y);
-        sm[pad(e + 1)] = make_float2(buf[i].z, buf[i].w);
+        dst[pad(e)] = make_float2(buf[i].x, buf[i].y);
+        dst[pad(e + 1)] = make_float2(buf[i].z, buf[i].w);
       }
     }
-  }
-  __syncthreads();
-  if constexpr (TWS) {
-    MidTwHookS<true> h{lohi, lohi + ROWS * 16, LGN1S, make_float2(1.f, 0.f)};
-    tile_fft<-1, TILE, NT, true>(sm, lay, tws, lgN1, h);
-  } else {
-    MidTwHook<true> h{g, u0, rt[0], make_float2(1.f, 0.f)};
-    tile_fft<-1, TILE, NT, false>(sm, lay, g.tw1, lgN1 + 1, h);
-  }
-
-  // spectrum operator over all (k, N-k) pairs held by this CTA
+    __syncthreads();
+  };
+  auto fwd_rows = [&](float2* buf) {
+    if constexpr (TWS) {
+      MidTwHookS<true> h{lohi, lohi + ROWS * 16, LGN1S, make_float2(1.f, 0.f)};
+      tile_fft<-1, TILE, NT, true>(buf, lay, tws, lgN1, h);
+    } else {
+      MidTwHook<true> h{g, u0, rt[0], make_float2(1.f, 0.f)};
+      tile_fft<-1, TILE, NT, false>(buf, lay, g.tw1, lgN1 + 1, h);
+    }
+  };
+  // Pair slot t of this CTA: elements ea (frequency k = k2 + N2 k1) and eb
+  // (frequency N - k) of the tile, table index tidx.
   const int nslots = (U << lgN1) + (u0 == 0 ? 1 : 0);
   const int base_u1 = ((g.N2 >> 1) - 1) << lgN1;   // table offset of unit 0
-  for (int t = threadIdx.x; t < nslots; t += NT) {
+  auto slot_at = [&](int t, int& ea, int& eb, int& k2, int& k1, int& tidx) {
     int ul, q;
     if (t < (U << lgN1)) { ul = t >> lgN1; q = t & (N1 - 1); }
     else { ul = 0; q = N1; }
     const int u = u0 + ul;
-    int ea, eb, k2, k1, tidx;
     if (u > 0) {
       k2 = u; k1 = q;
       ea = ((2 * ul) << lgN1) + q;
@@ -236,13 +237,79 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
       eb = ((2 * ul + 1) << lgN1) + (N1 - 1 - qq);
       tidx = base_u1 + q;
     }
-    float2 za = sm[pad(ea)], zb = sm[pad(eb)];
-    if (KIND == MID_ADMM) op_admm(kp.pp, a_rho, a_sigma, tidx, za, zb);
-    else op_real<KIND == MID_ADJ>(kp.pp, tidx, za, zb);
-    sm[pad(eb)] = zb;   // self-pairs (ea == eb) keep the k-side value
-    sm[pad(ea)] = za;
+  };
+
+  if constexpr (KIND == MID_CORR) {
+    // Spectra of two packed real vectors a (W) and b (W2).  From the pair
+    // (Z_k, Z_{N-k}) of a packed spectrum: E = (Z_k + conj Z_{N-k}) / 2,
+    // O = (Z_k - conj Z_{N-k}) / 2i, and the length-2N real spectrum is
+    // a^_k = E + w O, a^_{k+N} = E - w O, w = exp(-2 pi i k / 2N).
+    float2* sm2 = sm + smem_slots(TILE);
+    load_tile(sm, W);
+    fwd_rows(sm);
+    load_tile(sm2, kp.pp.W2);
+    fwd_rows(sm2);
+    const float sgn = (kp.flags & FL_PAIR2) ? -1.f : 1.f;
+    for (int t = threadIdx.x; t < nslots; t += NT) {
+      int ea, eb, k2, k1, tidx;
+      slot_at(t, ea, eb, k2, k1, tidx);
+      const float2 w = cmul(__ldg(g.twr + k2), __ldg(g.tw1 + k1));
+      float2 sa[2], sb[2];
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const float2* bufv = v ? sm2 : sm;
+        const float2 za = bufv[pad(ea)], zb = bufv[pad(eb)];
+        const float2 E = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+        const float2 O = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+        const float2 wo = cmul(w, O);
+        float2* dst = v ? sb : sa;
+        dst[0] = cadd(E, wo);
+        dst[1] = csub(E, wo);
+      }
+      const float2 p0 = cmulc(sb[0], sa[0]), p1 = cmulc(sb[1], sa[1]);   // conj(a^) b^
+      float4 acc = kp.pp.gacc[tidx];
+      acc.x = fmaf(sgn, p0.x, acc.x);
+      acc.y = fmaf(sgn, p0.y, acc.y);
+      acc.z = fmaf(sgn, p1.x, acc.z);
+      acc.w = fmaf(sgn, p1.y, acc.w);
+      kp.pp.gacc[tidx] = acc;
+    }
+    return;
+  } else if constexpr (KIND == MID_FROM_ACC) {
+    // The packed spectrum of the real vector d whose length-2N spectrum is
+    // gacc (D_k, D_{k+N} per slot), times tau / N for the unnormalised
+    // inverse:  E' = (D_k + D_{k+N}) / 2,  O' = conj(w) (D_k - D_{k+N}) / 2,
+    // Z'_k = E' + i O',  Z'_{N-k} = conj(E') + i conj(O').
+    const float sc = kp.ca->tau / (float)g.N;
+    for (int t = threadIdx.x; t < nslots; t += NT) {
+      int ea, eb, k2, k1, tidx;
+      slot_at(t, ea, eb, k2, k1, tidx);
+      const float2 w = cmul(__ldg(g.twr + k2), __ldg(g.tw1 + k1));
+      const float4 d = kp.pp.gacc[tidx];
+      const float2 d0 = make_float2(d.x, d.y), d1 = make_float2(d.z, d.w);
+      const float2 E = cscale(cadd(d0, d1), 0.5f);
+      const float2 O = cscale(cmulc(csub(d0, d1), w), 0.5f);
+      const float2 za = make_float2(E.x - O.y, E.y + O.x);
+      const float2 zb = make_float2(E.x + O.y, O.x - E.y);
+      sm[pad(eb)] = cscale(zb, sc);   // self-pairs (ea == eb): both sides agree
+      sm[pad(ea)] = cscale(za, sc);
+    }
+    __syncthreads();
+  } else {
+    load_tile(sm, W);
+    fwd_rows(sm);
+    // spectrum operator over all (k, N-k) pairs held by this CTA
+    for (int t = threadIdx.x; t < nslots; t += NT) {
+      int ea, eb, k2, k1, tidx;
+      slot_at(t, ea, eb, k2, k1, tidx);
+      float2 za = sm[pad(ea)], zb = sm[pad(eb)];
+      if (KIND == MID_ADMM) op_admm(kp.pp, a_rho, a_sigma, tidx, za, zb);
+      else op_real<KIND == MID_ADJ>(kp.pp, tidx, za, zb);
+      sm[pad(eb)] = zb;   // self-pairs (ea == eb) keep the k-side value
+      sm[pad(ea)] = za;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if constexpr (TWS) {
     MidTwHookS<false> h{lohi, lohi + ROWS * 16, LGN1S, make_float2(1.f, 0.f)};
     tile_fft<+1, TILE, NT, true>(sm, lay, tws, lgN1, h);
@@ -265,11 +332,16 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
 
 }  // namespace
 
-#define CS_MID_KINDS(X, T, S) X(MID_FWD, T, S) X(MID_ADJ, T, S) X(MID_ADMM, T, S)
+#define CS_MID_KINDS(X, T, S) \
+  X(MID_FWD, T, S) X(MID_ADJ, T, S) X(MID_ADMM, T, S) X(MID_CORR, T, S) X(MID_FROM_ACC, T, S)
+
+// MID_CORR holds two tiles in shared memory
+constexpr int mid_smem_mult(int kind) { return kind == MID_CORR ? 2 : 1; }
 
 cudaError_t init_mid_kernels() {
   cudaError_t e = cudaSuccess;
-#define CS_SET_MID(k, T, S) if (e == cudaSuccess) e = set_smem(mid_kernel<k, T, S>, T, Cfg<T>::MINB);
+#define CS_SET_MID(k, T, S) \
+  if (e == cudaSuccess) e = set_smem(mid_kernel<k, T, S>, T, Cfg<T>::MINB, mid_smem_mult(k));
   CS_MID_KINDS(CS_SET_MID, 4096, 0)
   CS_MID_KINDS(CS_SET_MID, 8192, 0)
   CS_MID_KINDS(CS_SET_MID, 4096, 1)
@@ -286,7 +358,7 @@ cudaError_t launch_mid(MidKind kind, const KParams& kp, cudaStream_t s) {
   if (g.lgN1 == 10 && g.lgU == 1 && g.tile == 4096) shape = 1;
   if (g.lgN1 == 11 && g.lgU == 0 && g.tile == 4096) shape = 2;
   if (g.lgN1 == 12 && g.lgU == 0 && g.tile == 8192) shape = 3;
-#define CS_L_MID(k, T, S) case k: return launch_k(mid_kernel<k, T, S>, grid, T, kp, s);
+#define CS_L_MID(k, T, S) case k: return launch_k(mid_kernel<k, T, S>, grid, T, kp, s, mid_smem_mult(k));
   switch (shape) {
     case 1: switch (kind) { CS_MID_KINDS(CS_L_MID, 4096, 1) } break;
     case 2: switch (kind) { CS_MID_KINDS(CS_L_MID, 4096, 2) } break;

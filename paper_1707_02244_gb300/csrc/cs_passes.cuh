@@ -96,9 +96,27 @@ struct RowSel {
 // Which epilogues look up the row mask, and how many mask bits one element
 // of the tile holds (2 in the packed real-FFT geometry, 1 in complex-n).
 template <int KIND> struct UsesMask {
-  static constexpr int kBits = (KIND == COL_RESIDUAL || KIND == COL_MASK) ? 2
+  static constexpr int kBits = (KIND == COL_RESIDUAL || KIND == COL_MASK || KIND == COL_RES_SAVE ||
+                                KIND == COL_GRAD_MASK) ? 2
                               : (KIND == COL_ADMM || KIND == COL_ADMM_LAST) ? 1 : 0;
 };
+
+// Block sum of one per-thread value, added to dst[blockIdx.x] (one slot per
+// CTA, so repeated launches accumulate without atomics; fixed order).
+template <int NT>
+__device__ void block_accum(float v, double* dst) {
+  __shared__ double red[NT / 32];
+  double d = (double)v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    dst[blockIdx.x] += s;
+  }
+}
 
 __device__ __forceinline__ float2 ld2(const float* p, int i) {
   return __ldg(reinterpret_cast<const float2*>(p) + i);
@@ -263,6 +281,97 @@ template <bool FWD> struct EpiAdmm {
 template <> struct Epi<COL_ADMM> : EpiAdmm<true> {};
 template <> struct Epi<COL_ADMM_LAST> : EpiAdmm<false> {};
 
+// ------------------------------------------------ unrolled-ISTA gradient
+// Reverse mode of T steps x(t+1) = eta_theta(u(t)), u(t) = x(t) + tau C^T r(t),
+// r(t) = M (P^T y - C x(t)).  With g = dL/dx(t+1) and w = g on the support
+// of x(t+1) (the support of the soft threshold's derivative: x(t+1) != 0
+// exactly when |u(t)| > theta, and then sign u(t) = sign x(t+1)):
+//   dL/dx(t) = w - tau C^T M C w,  dL/dtheta += -sum sign(x(t+1)) w,
+//   dL/dy += tau P C w,  dL/dc_k += tau sum_i (r_i w_{i+k} - q_i x(t)_{i+k})
+// with q = M C w.  CallArgs of one step: x = x(t), z = x(t+1), v = r(t),
+// mu = w, nu = q, dst = g, aux = dL/dy (compact, tile order of the rows); all
+// n-vectors packed float2 in tile order.
+
+template <> struct Epi<COL_LOADT> {
+  static constexpr bool kRead = false, kFwd = true;
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2, int p, int t, Acc&) {
+    return ld2(a.x, t);
+  }
+};
+
+template <> struct Epi<COL_RES_SAVE> {
+  static constexpr bool kRead = true, kFwd = true;
+  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2 v, int p, int t, Acc& acc) {
+    RowSel rs{acc.smask, acc.spref, acc.wbase};
+    int i0;
+    const uint32_t mm = rs.get2(t, i0);
+    const float r0 = (mm & 1u) ? __ldg(kp.pp.ys + i0) - v.x : 0.f;
+    const float r1 = (mm & 2u) ? __ldg(kp.pp.ys + i0 + (int)(mm & 1u)) - v.y : 0.f;
+    const float2 r = make_float2(r0, r1);
+    reinterpret_cast<float2*>(a.v)[t] = r;
+    return r;
+  }
+};
+
+template <> struct Epi<COL_ISTA_SEG> {
+  static constexpr bool kRead = true, kFwd = true;
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2 g, int p, int t, Acc&) {
+    const float2 xo = ld2(a.x, t);
+    const float2 xn = make_float2(soft(fmaf(a.tau, g.x, xo.x), a.thr), soft(fmaf(a.tau, g.y, xo.y), a.thr));
+    reinterpret_cast<float2*>(a.z)[t] = xn;
+    return xn;
+  }
+};
+
+__device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
+
+template <> struct Epi<COL_GRAD_W> {
+  static constexpr bool kRead = false, kFwd = true;
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2, int p, int t, Acc& acc) {
+    const float2 g = ld2(a.dst, t), xn = ld2(a.z, t);
+    const float2 w = make_float2(xn.x != 0.f ? g.x : 0.f, xn.y != 0.f ? g.y : 0.f);
+    acc.v[0] -= sgnf(xn.x) * w.x + sgnf(xn.y) * w.y;
+    reinterpret_cast<float2*>(a.mu)[t] = w;
+    return w;
+  }
+};
+
+template <> struct Epi<COL_GRAD_MASK> {
+  static constexpr bool kRead = true, kFwd = true;
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2 v, int p, int t, Acc& acc) {
+    RowSel rs{acc.smask, acc.spref, acc.wbase};
+    int i0;
+    const uint32_t mm = rs.get2(t, i0);
+    // each compact row index belongs to one element: plain read-modify-write
+    if (mm & 1u) a.aux[i0] = fmaf(a.tau, v.x, a.aux[i0]);
+    if (mm & 2u) a.aux[i0 + (int)(mm & 1u)] = fmaf(a.tau, v.y, a.aux[i0 + (int)(mm & 1u)]);
+    const float2 q = make_float2((mm & 1u) ? v.x : 0.f, (mm & 2u) ? v.y : 0.f);
+    reinterpret_cast<float2*>(a.nu)[t] = q;
+    return q;
+  }
+};
+
+template <> struct Epi<COL_GRAD_G> {
+  static constexpr bool kRead = true, kFwd = false;
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2 v, int p, int t, Acc&) {
+    const float2 w = ld2(a.mu, t);
+    const float2 g = make_float2(fmaf(-a.tau, v.x, w.x), fmaf(-a.tau, v.y, w.y));
+    reinterpret_cast<float2*>(a.dst)[t] = g;
+    return g;
+  }
+};
+
+// (r, w) -> (W, W2); with FL_PAIR2 (q, x(t)) -> (W, W2)
+template <> struct Epi<COL_LOAD2> {
+  static constexpr bool kRead = false, kFwd = true;
+  __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2, int p, int t, Acc&) {
+    return ld2((kp.flags & FL_PAIR2) ? a.nu : a.v, t);
+  }
+  __device__ static float2 apply2(const KParams& kp, const CallArgs& a, int t) {
+    return ld2((kp.flags & FL_PAIR2) ? a.x : a.mu, t);
+  }
+};
+
 template <int TILE> struct Cfg {
   static constexpr int NT = TILE / EPT;                 // threads per CTA
   static constexpr int MINB = 65536 / (64 * NT);        // mid pass: CTAs per SM at <= 64 registers
@@ -279,11 +388,11 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename K>
-cudaError_t launch_k(K kern, int grid, int tile, const KParams& kp, cudaStream_t s) {
+cudaError_t launch_k(K kern, int grid, int tile, const KParams& kp, cudaStream_t s, int smem_mult = 1) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(tile / EPT);
-  cfg.dynamicSmemBytes = pass_smem_bytes(tile);
+  cfg.dynamicSmemBytes = smem_mult * pass_smem_bytes(tile);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -297,13 +406,14 @@ cudaError_t launch_k(K kern, int grid, int tile, const KParams& kp, cudaStream_t
 // large enough for `ctas` resident CTAs, leaving the rest of the unified
 // L1 / shared array to L1 (where the twiddle tables live).
 template <typename K>
-cudaError_t set_smem(K kern, int tile, int ctas) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem_bytes(tile));
+cudaError_t set_smem(K kern, int tile, int ctas, int smem_mult = 1) {
+  const size_t dyn = smem_mult * pass_smem_bytes(tile);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e != cudaSuccess) return e;
   cudaFuncAttributes fa;
   e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return e;
-  const size_t per_cta = pass_smem_bytes(tile) + fa.sharedSizeBytes + 1024;
+  const size_t per_cta = dyn + fa.sharedSizeBytes + 1024;
   int pct = (int)((per_cta * ctas * 100 + 228 * 1024 - 1) / (228 * 1024));
   if (pct > 100) pct = 100;
   return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);

@@ -1,0 +1,163 @@
+"""GPU parity of cs_grad (reverse mode of unrolled ISTA) against the FP64
+oracle gradient and against central finite differences of the GPU forward.
+
+Both sides get the same dL/dx(T) (from the oracle's x(T)), so the comparison
+isolates the reverse pass.  The fp32 forward can take a different branch of
+the soft threshold than the FP64 one where |u| is within rounding of tau
+lambda; such flips perturb the gradient locally, so the bar is relative l2
+<= 1e-3 (measured errors are printed by the assertion messages).
+"""
+import numpy as np
+import pytest
+
+import oracle.cs_oracle as O
+import synth
+from gpu_util import f32, host, rel_l2, to_dev, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def cs():
+    import paper_1707_02244_gb300 as cs
+    return cs
+
+
+def _setup(n, m, k, seed, lam_scale=0.05):
+    inst = synth.instance(n, m, k=k, noise_std=1e-3, seed=seed)
+    chat = O.spectrum(inst.c)
+    y32 = (O.forward_fft(chat, inst.rows, inst.x_true) + inst.noise).astype(np.float32)
+    tau = f32(0.9 / np.max(np.abs(chat) ** 2))
+    lam = f32(lam_scale * np.max(np.abs(O.adjoint_fft(chat, inst.rows, y32.astype(np.float64)))))
+    return inst, y32, lam, tau
+
+
+def _gpu_grad(cs, inst, y32, lam, tau, T, K, gx):
+    torch, dev = torch_dev()
+    plan = cs.cs_plan(inst.n, inst.m, inst.rows, inst.c, torch.cuda.current_stream(dev))
+    try:
+        dc = torch.empty(inst.n, dtype=torch.float32, device=dev)
+        dl = torch.empty(1, dtype=torch.float32, device=dev)
+        dy = torch.empty(inst.m, dtype=torch.float32, device=dev)
+        cs.cs_grad(plan, to_dev(y32), lam, tau, T, K, to_dev(gx), dc, dl, dy)
+        assert cs.cs_status_sync(plan) == cs.CS_OK
+        return host(dc), float(host(dl)[0]), host(dy)
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("n,m,k,T,K", [(4096, 1024, 40, 50, 7), (1 << 14, 4000, 150, 40, 40),
+                                       (256, 100, 4, 1, 1), (1 << 16, 1 << 14, 600, 60, 25)])
+def test_grad_matches_oracle(cs, n, m, k, T, K):
+    inst, y32, lam, tau = _setup(n, m, k, 8000 + n + T)
+    y64 = y32.astype(np.float64)
+    xT = O.ista_fft(inst.c, inst.rows, y64, lam, tau, T)
+    gx = (2.0 * (xT - inst.x_true)).astype(np.float32)
+    o = O.ista_unrolled_grad_fft(inst.c, inst.rows, y64, lam, tau, T, gx.astype(np.float64))
+    dc, dl, dy = _gpu_grad(cs, inst, y32, lam, tau, T, K, gx)
+    assert rel_l2(dc, o["dc"]) <= GRAD_TOL, ("dc", rel_l2(dc, o["dc"]))
+    assert rel_l2(dy, o["dy"]) <= GRAD_TOL, ("dy", rel_l2(dy, o["dy"]))
+    assert abs(dl - o["dlam"]) <= GRAD_TOL * max(abs(o["dlam"]), 1e-12), ("dlam", dl, o["dlam"])
+
+
+def test_grad_is_deterministic_and_checkpoint_independent(cs):
+    """Same gradient for K = 5 and K = T (replay from the start), bit for bit
+    across repeated calls."""
+    inst, y32, lam, tau = _setup(2048, 700, 20, 8100)
+    xT = O.ista_fft(inst.c, inst.rows, y32.astype(np.float64), lam, tau, 30)
+    gx = (2.0 * (xT - inst.x_true)).astype(np.float32)
+    a = _gpu_grad(cs, inst, y32, lam, tau, 30, 5, gx)
+    b = _gpu_grad(cs, inst, y32, lam, tau, 30, 5, gx)
+    c = _gpu_grad(cs, inst, y32, lam, tau, 30, 30, gx)
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1] and np.array_equal(a[2], b[2])
+    assert np.array_equal(a[0], c[0]) and a[1] == c[1] and np.array_equal(a[2], c[2])
+
+
+def test_grad_finite_differences(cs):
+    """Directional derivatives of L = ||x(T) - x*||^2 (GPU forward, loss in
+    FP64) by central differences with eps = 1e-3 against cs_grad."""
+    torch, dev = torch_dev()
+    n, m, T, eps = 4096, 1024, 40, 1e-3
+    inst, y32, lam, tau = _setup(n, m, 40, 8200)
+    g = synth.rng(8201)
+
+    def loss(c, y, lm):
+        plan = cs.cs_plan(n, m, inst.rows, c, torch.cuda.current_stream(dev))
+        try:
+            x = torch.zeros(n, dtype=torch.float32, device=dev)
+            cs.cs_ista(plan, to_dev(y), f32(lm), tau, T, x)
+            d = host(x) - inst.x_true
+            return float(d @ d), d
+        finally:
+            plan.close()
+
+    L0, d0 = loss(inst.c, y32, lam)
+    dc, dl, dy = _gpu_grad(cs, inst, y32, lam, tau, T, 8, (2.0 * d0).astype(np.float32))
+    u = g.standard_normal(n) * np.linalg.norm(inst.c) / np.sqrt(n)
+    fd = (loss(inst.c + eps * u, y32, lam)[0] - loss(inst.c - eps * u, y32, lam)[0]) / (2 * eps)
+    assert abs(fd - dc @ u) <= 2e-2 * abs(fd) + 1e-6, ("c", fd, dc @ u)
+    v = (g.standard_normal(m) * np.linalg.norm(y32) / np.sqrt(m)).astype(np.float32)
+    fd = (loss(inst.c, y32 + np.float32(eps) * v, lam)[0] - loss(inst.c, y32 - np.float32(eps) * v, lam)[0]) / (2 * eps)
+    assert abs(fd - dy @ v) <= 2e-2 * abs(fd) + 1e-6, ("y", fd, dy @ v)
+    h = eps * lam
+    fd = (loss(inst.c, y32, lam + h)[0] - loss(inst.c, y32, lam - h)[0]) / (2 * h)
+    assert abs(fd - dl) <= 2e-2 * abs(fd) + 1e-6, ("lambda", fd, dl)
+
+
+def test_grad_full_configuration(cs):
+    """Unrolled ISTA T = 300 on n = 2^20, m = n/4, checkpoints every 25
+    steps, loss ||x(T) - x*||^2, against the FP64 oracle gradient.
+
+    At this size the gradient's own conditioning sets the floor: s is how far
+    the FP64 oracle gradient moves when the inputs the fp32 path rounds (y
+    and the spectrum of c, held as fp32 tables) are perturbed once at the
+    fp32 rounding level (relative 2^-24).  The fp32 path rounds afresh at
+    each of the T steps; as a random walk that grows like sqrt(T), so the bar
+    is max(1e-3, sqrt(T) s)."""
+    n, T, K = 1 << 20, 300, 25
+    inst = synth.instance(n, n // 4, k=n // 100, noise_std=1e-3, seed=8300)
+    chat = O.spectrum(inst.c)
+    y32 = (O.forward_fft(chat, inst.rows, inst.x_true) + inst.noise).astype(np.float32)
+    y64 = y32.astype(np.float64)
+    tau = f32(0.9 / np.max(np.abs(chat) ** 2))
+    lam = f32(5e-3)
+    xT = O.ista_fft(inst.c, inst.rows, y64, lam, tau, T)
+    gx = (2.0 * (xT - inst.x_true)).astype(np.float32)
+    o = O.ista_unrolled_grad_fft(inst.c, inst.rows, y64, lam, tau, T, gx.astype(np.float64))
+    g = synth.rng(8301)
+    yp = y64 * (1.0 + 2.0 ** -24 * g.standard_normal(y64.shape))
+    ch = np.fft.rfft(inst.c)
+    cp = np.fft.irfft(ch * (1.0 + 2.0 ** -24 * (g.standard_normal(ch.shape) + 1j * g.standard_normal(ch.shape))), n)
+    op = O.ista_unrolled_grad_fft(cp, inst.rows, yp, lam, tau, T, gx.astype(np.float64))
+    sens = {"dc": rel_l2(op["dc"], o["dc"]), "dy": rel_l2(op["dy"], o["dy"]),
+            "dlam": abs(op["dlam"] - o["dlam"]) / abs(o["dlam"])}
+    dc, dl, dy = _gpu_grad(cs, inst, y32, lam, tau, T, K, gx)
+    err = {"dc": rel_l2(dc, o["dc"]), "dy": rel_l2(dy, o["dy"]), "dlam": abs(dl - o["dlam"]) / abs(o["dlam"])}
+    for key in err:
+        assert err[key] <= max(GRAD_TOL, np.sqrt(T) * sens[key]), (key, err, sens)
+
+
+def test_unrolled_ista_autograd_function(cs):
+    """torch.autograd through UnrolledISTA: the gradients of
+    ||x(T) - x*||^2 equal the oracle's (loss formed in torch)."""
+    torch, dev = torch_dev()
+    inst, y32, lam, tau = _setup(2048, 600, 15, 8400)
+    T, K = 25, 6
+    c = torch.tensor(inst.c, dtype=torch.float64, device=dev, requires_grad=True)
+    y = to_dev(y32).requires_grad_(True)
+    lam_t = torch.tensor(lam, dtype=torch.float32, device=dev, requires_grad=True)
+    x = cs.UnrolledISTA.apply(c, y, lam_t, inst.rows, tau, T, K)
+    xs = to_dev(inst.x_true)
+    loss = ((x - xs) ** 2).sum()
+    loss.backward()
+    # the oracle takes its own x(T) for dL/dx(T); both sides' x(T) agree to
+    # fp32 rounding, so the gradients differ by that much at most
+    y64 = y32.astype(np.float64)
+    xo = O.ista_fft(inst.c, inst.rows, y64, lam, tau, T)
+    o = O.ista_unrolled_grad_fft(inst.c, inst.rows, y64, lam, tau, T, 2.0 * (xo - inst.x_true))
+    assert rel_l2(host(x), xo) <= 1e-5
+    assert rel_l2(host(c.grad), o["dc"]) <= GRAD_TOL
+    assert rel_l2(host(y.grad), o["dy"]) <= GRAD_TOL
+    assert abs(float(lam_t.grad) - o["dlam"]) <= GRAD_TOL * abs(o["dlam"])

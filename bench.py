@@ -15,6 +15,7 @@ spectrum, tables) and the power iteration are set-up, reported separately.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--iters T] [--impl reference]
   python bench.py --workload batched [--steps K] [--warmup W] [--iters T]
   python bench.py --workload grad [--steps K] [--warmup W]
+  python bench.py --workload context
 
 The batched workload: 512 independent instances, n log-uniform in
 [2^12, 2^20] (snapped to powers of two), m/n uniform in [0.2, 0.5], k/n =
@@ -59,7 +60,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=1 << 22)
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-NMSE, roofline and CPU legs")
-    ap.add_argument("--workload", default="n2e22", choices=["n2e22", "batched", "grad"])
+    ap.add_argument("--workload", default="n2e22", choices=["n2e22", "batched", "grad", "context"])
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched workload")
     return ap.parse_args()
 
@@ -207,16 +208,24 @@ def pass_bytes(pid, n, m):
     return 16 * n + 16 * n + 4 * m + n // 4   # ADMM column pass: W, mu, nu in/out, y, mask
 
 
+PASS_SOURCES = ("cs_col.cu", "cs_mid.cu", "cs_passes.cuh", "cs_fft.cuh", "cs_internal.h")
+
+
+def pass_sources_digest():
+    """sha256[:16] of the sources that define the pass kernels."""
+    src = hashlib.sha256()
+    for name in PASS_SOURCES:
+        src.update((ROOT / "paper_1707_02244_gb300" / "csrc" / name).read_bytes())
+    return src.hexdigest()[:16]
+
+
 def traffic_record(pid):
     """ncu DRAM bytes per launch from profiles/dram_traffic.txt, valid only
     while the kernel sources are unchanged."""
     f = ROOT / "profiles" / "dram_traffic.txt"
     if not f.exists():
         return None
-    src = hashlib.sha256()
-    for p in sorted((ROOT / "paper_1707_02244_gb300" / "csrc").glob("*")):
-        src.update(p.read_bytes())
-    digest = src.hexdigest()[:16]
+    digest = pass_sources_digest()
     for ln in f.read_text().splitlines():
         parts = ln.split()
         if len(parts) >= 4 and parts[0] == "pass" and parts[1] == str(pid) and parts[3] == digest:
@@ -606,6 +615,85 @@ def run_grad(args):
     return 0
 
 
+def run_context(args):
+    """Context for the paper's own claims, re-run on GB300 with synthetic data.
+    (1) Square circulant products C x (m = n): the direct scheme (one O(n)
+    dot product per row, cs_forward_direct) against the FFT path
+    (cs_forward on a plan keeping every row), n = 2^10 .. 2^18.
+    (2) Recovery error over time at n = 2^15 (m = n/2, k = n/10, c ~
+    N(0,1/m), noise 1e-3, lambda = 1e-2): NMSE against x* after t iterations
+    of ISTA and of ADMM (rho = 1), with the plan time (spectrum and tables,
+    the counterpart of the paper's initial inversion) added to each solve."""
+    import torch
+    import paper_1707_02244_gb300 as cs
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def dev_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    products = []
+    for lg in range(10, 19, 2):
+        n = 1 << lg
+        g = synth.rng(9100 + lg)
+        c = synth.gaussian_c(g, n, n)
+        x = torch.from_numpy(g.standard_normal(n).astype(np.float32)).to(dev)
+        y = torch.empty(n, dtype=torch.float32, device=dev)
+        rows = torch.arange(n, dtype=torch.int32, device=dev)
+        c32 = torch.from_numpy(c.astype(np.float32)).to(dev)
+        plan = cs.cs_plan(n, n, np.arange(n), c, stream)
+        reps = 20 if lg <= 16 else 5
+        t_fft = dev_ms(lambda: cs.cs_forward(plan, x, y), reps)
+        t_dir = dev_ms(lambda: cs.cs_forward_direct(n, n, c32, rows, x, y, stream), reps)
+        plan.close()
+        products.append({"n": n, "fft_us": 1e3 * t_fft, "direct_us": 1e3 * t_dir, "direct_over_fft": t_dir / t_fft})
+
+    n = 1 << 15
+    m = n // 2
+    inst = synth.instance(n, m, k=n // 10, noise_std=1e-3, seed=9200)
+    lam = 1e-2
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = cs.cs_plan(n, m, inst.rows, inst.c, stream)
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    xt = torch.from_numpy(inst.x_true.astype(np.float32)).to(dev)
+    y = torch.empty(m, dtype=torch.float32, device=dev)
+    cs.cs_forward(plan, xt, y)
+    y += torch.from_numpy(inst.noise.astype(np.float32)).to(dev)
+    t0 = time.perf_counter()
+    tau = float(np.float32(1.0 / cs.cs_opnorm2(plan, 100)))
+    opnorm_ms = 1e3 * (time.perf_counter() - t0)
+    cs.cs_set_monitor(plan, xt, 0.0, 10)
+    curve = {"ista": [], "admm": []}
+    for it in (1, 2, 5, 10, 20, 50, 100, 200, 500, 1000, 2000):
+        x = torch.zeros(n, dtype=torch.float32, device=dev)
+        z = torch.zeros(n, dtype=torch.float32, device=dev)
+        si = cs.cs_ista(plan, y, lam, tau, it, x)
+        sa = cs.cs_admm(plan, y, lam, 1.0, it, z)
+        curve["ista"].append({"iters": it, "solve_ms": si["ms"], "ms_incl_setup": plan_ms + opnorm_ms + si["ms"],
+                              "nmse": si["nmse"]})
+        curve["admm"].append({"iters": it, "solve_ms": sa["ms"], "ms_incl_setup": plan_ms + sa["ms"],
+                              "nmse": sa["nmse"]})
+    plan.close()
+    line = {"metric": "context: direct vs FFT circulant product; NMSE over time ISTA vs ADMM at n=2^15",
+            "products": products,
+            "curve": {"n": n, "m": m, "k": n // 10, "lambda": lam, "tau": tau, "plan_ms": plan_ms,
+                      "opnorm_ms_100_iters": opnorm_ms, **curve},
+            "dtype": "f32", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -614,6 +702,8 @@ def main():
         return run_batched(args)
     if args.workload == "grad":
         return run_grad(args)
+    if args.workload == "context":
+        return run_context(args)
     return run_gpu(args)
 
 

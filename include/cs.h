@@ -218,6 +218,15 @@ cs_status cs_batch_admm(cs_batch_t batch, const float* y, const float* lambda,
  * not finite, else the first error latched by a per-instance plan. */
 cs_status cs_batch_status_sync(cs_batch_t batch);
 
+/* Direct circulant product (context comparator; Sec. 5.2's scheme of one
+ * O(n) dot product per output, not the FFT path).  No plan:
+ *   c     DEVICE float[n]: first row of C (fp32)
+ *   rows  DEVICE int32[m]: kept rows, 0 <= rows[i] < n (not checked)
+ *   x     DEVICE float[n];  y DEVICE float[m] receives (A x)_i = (C x)_{rows[i]}
+ * O(m n) work, one warp per row.  Asynchronous on `stream`. */
+cs_status cs_forward_direct(int64_t n, int64_t m, const float* c, const int32_t* rows,
+                            const float* x, float* y, void* stream);
+
 /* Largest n accepted by cs_circulant_apply_static. */
 #define CS_STATIC_MAX_N 16384
 

@@ -26,7 +26,7 @@ EXPORTS = ("cs_plan", "cs_plan_destroy", "cs_opnorm2", "cs_forward", "cs_adjoint
            "cs_set_monitor", "cs_ista", "cs_admm", "cs_admm_ex", "cs_status_sync",
            "cs_status_string", "cs_version", "cs_profile_pass", "cs_circulant_apply_static",
            "cs_batch_plan", "cs_batch_destroy", "cs_batch_ista", "cs_batch_admm", "cs_batch_status_sync",
-           "cs_grad")
+           "cs_grad", "cs_forward_direct")
 
 
 class CsStats(ctypes.Structure):
@@ -71,6 +71,7 @@ def _load() -> ctypes.CDLL:
         "cs_profile_pass": [vp, ci, ci],
         "cs_circulant_apply_static": [i64, vp, vp, vp, ci, vp],
         "cs_grad": [vp, vp, f32, f32, ci, ci, vp, vp, vp, vp],
+        "cs_forward_direct": [i64, i64, vp, vp, vp, vp, vp],
         "cs_batch_plan": [ctypes.POINTER(vp), ci, vp, vp, vp, vp, vp],
         "cs_batch_destroy": [vp],
         "cs_batch_ista": [vp, vp, vp, vp, ci, vp],
@@ -262,6 +263,14 @@ def __getattr__(name):
         globals()["UnrolledISTA"] = cls
         return cls
     raise AttributeError(name)
+
+
+def cs_forward_direct(n: int, m: int, c, rows, x, y, stream=None):
+    """y = A x by one O(n) dot product per kept row (context comparator);
+    c float32 device (n,), rows int32 device (m,)."""
+    rptr = int(rows.data_ptr()) if hasattr(rows, "data_ptr") else int(rows)
+    _check(_lib.cs_forward_direct(int(n), int(m), _ptr(c), rptr, _ptr(x), _ptr(y), _stream_handle(stream)),
+           "cs_forward_direct")
 
 
 def cs_profile_pass(plan: Plan, pass_id: int, reps: int = 1):

@@ -107,3 +107,10 @@ def test_null_batch_is_an_argument_error(cs):
     assert cs.raw_call("cs_batch_ista", None, None, lam.ctypes.data, lam.ctypes.data, 1, None) == cs.CS_ERR_ARG
     assert cs.raw_call("cs_batch_admm", None, None, lam.ctypes.data, lam.ctypes.data, 1, None) == cs.CS_ERR_ARG
     assert cs.raw_call("cs_batch_status_sync", None) == cs.CS_ERR_ARG
+
+
+def test_direct_product_rejects_bad_arguments_without_device(cs):
+    buf = ctypes.c_void_p(8)
+    assert cs.raw_call("cs_forward_direct", 0, 1, buf, buf, buf, buf, None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_forward_direct", 16, 17, buf, buf, buf, buf, None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_forward_direct", 16, 4, None, buf, buf, buf, None) == cs.CS_ERR_ARG

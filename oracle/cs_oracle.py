@@ -41,6 +41,8 @@ __all__ = [
     "admm_d_diagonal", "opnorm2_dense", "opnorm2_power_fft",
     "lasso_bruteforce", "l0_bruteforce", "nmse", "naive_dft",
     "ista_unrolled_grad_dense", "ista_unrolled_grad_fft", "ista_unrolled_loss",
+    "circulant2d_matrix", "sensing2d_matrix", "spectrum2d", "circulant2d_apply_fft", "forward2d_fft",
+    "adjoint2d_fft", "ista_dense2d", "ista_fft2d", "admm_dense2d", "admm_fft2d", "naive_dft2",
 ]
 
 
@@ -491,3 +493,106 @@ def ista_unrolled_loss(c, rows, y, lam, tau, T, x_star, dense=True):
     xT = run(c, rows, y, lam, tau, T)
     d = xT - np.asarray(x_star, dtype=np.float64)
     return float(np.dot(d, d)), 2.0 * d
+
+
+# --------------------------------------------------------------------------
+# Two-dimensional operator (Sec. 7, compressed deblurring: A = P H with H the
+# periodic blur of an n0 x n1 image, a product of a sampling and a circulant
+# -- here block-circulant with circulant blocks -- matrix)
+# --------------------------------------------------------------------------
+#
+# Images are flattened row-major (pixel (a, b) is entry a n1 + b).  The blur
+# follows Sec. 4.2's index rule in both axes:
+#   (H x)[i0, i1] = sum_{j0, j1} c2[(j0 - i0) mod n0, (j1 - i1) mod n1] x[j0, j1]
+# so that, for real c2, DFT2(H x) = conj(DFT2 c2) DFT2 x and
+# DFT2(H^T x) = DFT2(c2) DFT2 x.  A convolution with a point-spread function
+# psf is H with c2[d] = psf[-d].
+
+def circulant2d_matrix(c2: np.ndarray) -> np.ndarray:
+    """Dense (n0 n1) x (n0 n1) matrix H of the 2D index rule above."""
+    c2 = np.asarray(c2, dtype=np.float64)
+    n0, n1 = c2.shape
+    a = np.arange(n0 * n1) // n1
+    b = np.arange(n0 * n1) % n1
+    return c2[(a[None, :] - a[:, None]) % n0, (b[None, :] - b[:, None]) % n1]
+
+
+def sensing2d_matrix(c2, pix) -> np.ndarray:
+    """A = P H: the rows ``pix`` (flattened pixel indices) of H."""
+    return circulant2d_matrix(c2)[np.asarray(pix, dtype=np.int64), :]
+
+
+def naive_dft2(v: np.ndarray) -> np.ndarray:
+    """O(n^2) 2D DFT by the 1D definition along each axis (no FFT library)."""
+    v = np.asarray(v, dtype=np.complex128)
+    rows = np.array([naive_dft(r) for r in v])
+    return np.array([naive_dft(col) for col in rows.T]).T
+
+
+def spectrum2d(c2: np.ndarray) -> np.ndarray:
+    """2D DFT of the generating array: the eigenvalues of H (conjugated)."""
+    return np.fft.fft2(np.asarray(c2, dtype=np.float64))
+
+
+def circulant2d_apply_fft(chat2, x, transpose=False):
+    """H x (or H^T x) of a flattened image by the 2D convolution theorem."""
+    n0, n1 = chat2.shape
+    xh = np.fft.rfft2(np.asarray(x, dtype=np.float64).reshape(n0, n1))
+    h = chat2[:, : n1 // 2 + 1]
+    h = h if transpose else np.conj(h)
+    return np.fft.irfft2(h * xh, (n0, n1)).ravel()
+
+
+def forward2d_fft(chat2, pix, x):
+    """A x = (H x)[pix]."""
+    return circulant2d_apply_fft(chat2, x)[np.asarray(pix, dtype=np.int64)]
+
+
+def adjoint2d_fft(chat2, pix, r):
+    """A^T r = H^T P^T r."""
+    n = chat2.size
+    return circulant2d_apply_fft(chat2, zero_fill(n, pix, r), transpose=True)
+
+
+def ista_dense2d(c2, pix, y, lam, tau, iters, x0=None, history=False):
+    """Algorithm 1 with the dense 2D sensing matrix (tiny images)."""
+    A = sensing2d_matrix(c2, pix)
+    y = np.asarray(y, dtype=np.float64)
+    return _ista(lambda v: A @ v, lambda r: A.T @ r, y, lam, tau, iters, x0, A.shape[1], history)
+
+
+def ista_fft2d(c2, pix, y, lam, tau, iters, x0=None, history=False):
+    """Algorithm 1 with the 2D products taken by FFT."""
+    chat2 = spectrum2d(c2)
+    y = np.asarray(y, dtype=np.float64)
+    return _ista(lambda v: forward2d_fft(chat2, pix, v), lambda r: adjoint2d_fft(chat2, pix, r), y, lam, tau,
+                 iters, x0, chat2.size, history)
+
+
+def admm_dense2d(c2, pix, y, lam, sigma, rho, tau1=1.0, tau2=1.0, iters=100, state=None, history=False):
+    """Algorithm 3 with the dense 2D blur H; B = (rho H^T H + sigma I)^-1 by
+    a dense Cholesky factor (tiny images)."""
+    H = circulant2d_matrix(c2)
+    n = H.shape[0]
+    L = np.linalg.cholesky(rho * (H.T @ H) + sigma * np.eye(n))
+
+    def B_apply(b):
+        return np.linalg.solve(L.T, np.linalg.solve(L, b))
+
+    return _admm(lambda v: H @ v, lambda v: H.T @ v, B_apply, n, pix, np.asarray(y, dtype=np.float64), lam,
+                 sigma, rho, tau1, tau2, iters, state, history)
+
+
+def admm_fft2d(c2, pix, y, lam, sigma, rho, tau1=1.0, tau2=1.0, iters=100, state=None, history=False):
+    """Algorithm 3 with the 2D blur: rho H^T H + sigma I is diagonalised by
+    the 2D DFT with eigenvalues rho |chat2|^2 + sigma."""
+    chat2 = spectrum2d(c2)
+    n0, n1 = chat2.shape
+    bhat = 1.0 / (rho * np.abs(chat2) ** 2 + sigma)
+
+    def B_apply(b):
+        return np.fft.irfft2(bhat[:, : n1 // 2 + 1] * np.fft.rfft2(b.reshape(n0, n1)), (n0, n1)).ravel()
+
+    return _admm(lambda v: circulant2d_apply_fft(chat2, v), lambda v: circulant2d_apply_fft(chat2, v, True),
+                 B_apply, n0 * n1, pix, np.asarray(y, dtype=np.float64), lam, sigma, rho, tau1, tau2, iters,
+                 state, history)

@@ -113,6 +113,56 @@ def batch_instances(n, m, *, k_frac: float = 0.01, noise_std: float = 1e-3, seed
             for i, (ni, mi) in enumerate(zip(n, m))]
 
 
+STAR_SEED = 1707002
+
+
+def gaussian_psf(sigma: float = 2.5, support: int = 15) -> np.ndarray:
+    """support x support Gaussian point-spread function, normalised to sum 1."""
+    h = support // 2
+    d = np.arange(-h, h + 1, dtype=np.float64)
+    g = np.exp(-0.5 * (d / sigma) ** 2)
+    psf = np.outer(g, g)
+    return psf / psf.sum()
+
+
+def psf_generator(psf: np.ndarray, n0: int, n1: int) -> np.ndarray:
+    """Generating array c2 (n0 x n1) of the periodic convolution with psf
+    (centred): c2[d] = psf[-d], indices mod (n0, n1)."""
+    c2 = np.zeros((n0, n1))
+    h0, h1 = psf.shape[0] // 2, psf.shape[1] // 2
+    for u in range(psf.shape[0]):
+        for v in range(psf.shape[1]):
+            c2[(h0 - u) % n0, (h1 - v) % n1] += psf[u, v]
+    return c2
+
+
+class Image2D:
+    """A 2D instance: image x (flattened row-major), generating array c2,
+    kept pixels pix (flattened indices, draw order), noise on y."""
+
+    def __init__(self, n0, n1, c2, pix, x_true, noise, seed):
+        self.n0, self.n1, self.c2, self.pix, self.x_true, self.noise, self.seed = n0, n1, c2, pix, x_true, noise, seed
+        self.n = n0 * n1
+        self.m = len(pix)
+
+
+def star_field(n0: int = 4096, n1: int = 4096, k: int = 20000, m_frac: float = 1.0 / 3.0,
+               noise_std: float = 1e-3, sigma_psf: float = 2.5, seed: int = STAR_SEED) -> Image2D:
+    """Sparse star field: k point sources at distinct uniform pixels with
+    log-normal(0, 1) fluxes, blurred periodically by a 15 x 15 Gaussian PSF
+    (sigma_psf), m = floor(m_frac n) pixels kept, noise N(0, noise_std^2)."""
+    g = rng(seed)
+    n = n0 * n1
+    x = np.zeros(n)
+    pos = g.choice(n, size=k, replace=False)
+    x[pos] = g.lognormal(0.0, 1.0, size=k)
+    c2 = psf_generator(gaussian_psf(sigma_psf), n0, n1)
+    m = int(np.floor(m_frac * n))
+    pix = draw_rows(g, n, m)
+    noise = g.standard_normal(m) * noise_std
+    return Image2D(n0, n1, c2, pix, x, noise, seed)
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     """Dense N(0,1) vector (operator tests)."""
     return rng(seed).standard_normal(n)

@@ -375,6 +375,80 @@ def check_unrolled_grad_dense_fft_agree(O):
     assert abs(fd - float(np.dot(gf["dc"], d))) <= 1e-6 * max(1.0, abs(fd))
 
 
+# ---------------------------------------------------------------- 2D operator
+
+def check_2d_separable_is_kronecker(O):
+    """A separable generating array c2 = c0 c1^T blurs rows and columns
+    independently: H = C(c0) kron C(c1), built from the pinned 1D circulant."""
+    g = synth.rng(151)
+    for n0, n1 in ((4, 8), (3, 5), (8, 4)):
+        c0, c1 = g.standard_normal(n0), g.standard_normal(n1)
+        H = O.circulant2d_matrix(np.outer(c0, c1))
+        K = np.kron(O.circulant_matrix(c0), O.circulant_matrix(c1))
+        assert np.allclose(H, K, atol=1e-13), (n0, n1)
+
+
+def check_2d_eigenvectors(O):
+    """H f = conj(chat2[k0, k1]) f for the 2D Fourier vectors
+    f = exp(2 pi i (j0 k0 / n0 + j1 k1 / n1)), chat2 by the O(n^2) definition
+    along both axes (no FFT library); spectrum2d equals it."""
+    g = synth.rng(152)
+    n0, n1 = 4, 6
+    c2 = g.standard_normal((n0, n1))
+    H = O.circulant2d_matrix(c2)
+    ch = O.naive_dft2(c2)
+    j0 = np.arange(n0 * n1) // n1
+    j1 = np.arange(n0 * n1) % n1
+    for k0 in range(n0):
+        for k1 in range(n1):
+            f = np.exp(2j * np.pi * (j0 * k0 / n0 + j1 * k1 / n1))
+            assert np.allclose(H @ f, np.conj(ch[k0, k1]) * f, atol=1e-12), (k0, k1)
+    assert np.allclose(O.spectrum2d(c2), ch, atol=1e-12)
+
+
+def check_2d_point_source_is_psf(O):
+    """Blurring a single bright pixel reproduces the point-spread function
+    around it (periodic), for the generating array of a non-symmetric PSF."""
+    n0, n1 = 16, 32
+    psf = synth.rng(153).random((5, 3))
+    psf /= psf.sum()
+    c2 = synth.psf_generator(psf, n0, n1)
+    a, b = 14, 1                      # near two edges: wrap-around
+    x = np.zeros(n0 * n1)
+    x[a * n1 + b] = 1.0
+    img = O.circulant2d_apply_fft(O.spectrum2d(c2), x).reshape(n0, n1)
+    want = np.zeros((n0, n1))
+    for u in range(5):
+        for v in range(3):
+            want[(a + u - 2) % n0, (b + v - 1) % n1] += psf[u, v]
+    assert np.allclose(img, want, atol=1e-14)
+
+
+def check_2d_fft_matches_dense(O):
+    """2D FFT products and both solvers equal their dense forms."""
+    g = synth.rng(154)
+    n0, n1 = 8, 16
+    c2 = g.standard_normal((n0, n1)) / 8
+    pix = synth.draw_rows(g, n0 * n1, 50)
+    A = O.sensing2d_matrix(c2, pix)
+    ch = O.spectrum2d(c2)
+    x = g.standard_normal(n0 * n1)
+    r = g.standard_normal(50)
+    assert np.allclose(O.forward2d_fft(ch, pix, x), A @ x, atol=1e-12)
+    assert np.allclose(O.adjoint2d_fft(ch, pix, r), A.T @ r, atol=1e-12)
+    xs = np.zeros(n0 * n1)
+    xs[g.choice(n0 * n1, 4, replace=False)] = g.standard_normal(4)
+    y = A @ xs
+    tau = 1.0 / np.linalg.norm(A, 2) ** 2
+    a = O.ista_dense2d(c2, pix, y, 1e-3, tau, 60)
+    b = O.ista_fft2d(c2, pix, y, 1e-3, tau, 60)
+    assert np.allclose(a, b, atol=1e-11)
+    a = O.admm_dense2d(c2, pix, y, 1e-3, 0.7, 1.3, iters=60)
+    b = O.admm_fft2d(c2, pix, y, 1e-3, 0.7, 1.3, iters=60)
+    for key in ("x", "z", "mu", "nu", "v"):
+        assert np.allclose(a[key], b[key], atol=1e-10), key
+
+
 ALL_CHECKS = [
     check_circulant_worked_example, check_eigenvalues_are_dft,
     check_fft_products_match_dense, check_adjoint_identity,
@@ -384,4 +458,6 @@ ALL_CHECKS = [
     check_admm_fixed_point_relations, check_bruteforce_lasso,
     check_exact_recovery_tiny, check_admm_inverse, check_dense_fft_agree,
     check_opnorm, check_unrolled_grad_finite_differences, check_unrolled_grad_dense_fft_agree,
+    check_2d_separable_is_kronecker, check_2d_eigenvectors, check_2d_point_source_is_psf,
+    check_2d_fft_matches_dense,
 ]

@@ -126,6 +126,30 @@ def _grad_variant(drop_q=False, active_from_x=False, dy_no_tau=False, dlam_sign=
     return _g
 
 
+def _mut_circulant2d_transposed(c2):
+    c2 = np.asarray(c2, dtype=np.float64)
+    n0, n1 = c2.shape
+    a = np.arange(n0 * n1) // n1
+    b = np.arange(n0 * n1) % n1
+    return c2[(a[:, None] - a[None, :]) % n0, (b[:, None] - b[None, :]) % n1]
+
+
+def _mut_circulant2d_axes_mixed(c2):
+    c2 = np.asarray(c2, dtype=np.float64)
+    n0, n1 = c2.shape
+    a = np.arange(n0 * n1) // n1
+    b = np.arange(n0 * n1) % n1
+    return c2[(a[None, :] - a[:, None]) % n0, (b[:, None] - b[None, :]) % n1]
+
+
+def _mut_c2d_apply_conj(chat2, x, transpose=False):
+    n0, n1 = chat2.shape
+    xh = np.fft.rfft2(np.asarray(x, dtype=np.float64).reshape(n0, n1))
+    h = chat2[:, : n1 // 2 + 1]
+    h = np.conj(h) if transpose else h
+    return np.fft.irfft2(h * xh, (n0, n1)).ravel()
+
+
 MUTANTS = {
     "transposed_circulant": ("circulant_matrix", _mut_transposed_circulant),
     "reverse_circulant": ("circulant_matrix", _mut_reverse_circulant),
@@ -143,6 +167,9 @@ MUTANTS = {
     "grad_dy_no_tau": ("_ista_grad", _grad_variant(dy_no_tau=True)),
     "grad_dlam_sign": ("_ista_grad", _grad_variant(dlam_sign=+1.0)),
     "grad_corr_swapped": ("_ista_grad", _grad_variant(corr_swap=True)),
+    "c2d_transposed": ("circulant2d_matrix", _mut_circulant2d_transposed),
+    "c2d_axes_mixed": ("circulant2d_matrix", _mut_circulant2d_axes_mixed),
+    "c2d_fft_conj_swapped": ("circulant2d_apply_fft", _mut_c2d_apply_conj),
 }
 
 

@@ -155,6 +155,22 @@ cs_status cs_admm_ex(cs_plan_t plan, const float* y, float lambda,
  * (pass_id, reps < 1, no earlier solve of that kind). */
 cs_status cs_profile_pass(cs_plan_t plan, int pass_id, int reps);
 
+/* Plan of the 2D operator (Sec. 7, compressed deblurring): A = P H with H
+ * the periodic blur of an n0 x n1 image, block-circulant with circulant
+ * blocks, following Sec. 4.2's index rule in both axes:
+ *   (H x)[i0][i1] = sum_{j0,j1} c2[(j0 - i0) mod n0][(j1 - i1) mod n1] x[j0][j1]
+ * (a convolution with a point-spread function psf is c2[d] = psf[-d]).
+ *   n0, n1  powers of two, 8 <= n0 <= 4096, 16 <= n1 <= 4096
+ *   pix     HOST int64[m]: kept pixels, flattened row-major (i0 n1 + i1),
+ *           distinct, in any order; y[i] pairs with pix[i]
+ *   c2      HOST float64[n0 n1], row-major
+ * The returned plan is used with cs_forward, cs_adjoint, cs_opnorm2,
+ * cs_set_monitor, cs_ista, cs_admm, cs_admm_ex on flattened images of
+ * n = n0 n1 values (cs_grad returns CS_ERR_UNSUPPORTED).  Errors as
+ * cs_plan. */
+cs_status cs_plan_2d(cs_plan_t* out, int64_t n0, int64_t n1, int64_t m, const int64_t* pix,
+                     const double* c2, void* stream);
+
 /* Gradient of unrolled ISTA (no counterpart in the paper: reverse mode
  * through T steps of Algorithm 1, for calibration of c, lambda or y by
  * gradient descent).  With x(0) = 0 and x(t+1) = eta_{tau lambda}(x(t) +

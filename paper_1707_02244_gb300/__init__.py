@@ -26,7 +26,7 @@ EXPORTS = ("cs_plan", "cs_plan_destroy", "cs_opnorm2", "cs_forward", "cs_adjoint
            "cs_set_monitor", "cs_ista", "cs_admm", "cs_admm_ex", "cs_status_sync",
            "cs_status_string", "cs_version", "cs_profile_pass", "cs_circulant_apply_static",
            "cs_batch_plan", "cs_batch_destroy", "cs_batch_ista", "cs_batch_admm", "cs_batch_status_sync",
-           "cs_grad", "cs_forward_direct")
+           "cs_grad", "cs_forward_direct", "cs_plan_2d")
 
 
 class CsStats(ctypes.Structure):
@@ -71,6 +71,7 @@ def _load() -> ctypes.CDLL:
         "cs_profile_pass": [vp, ci, ci],
         "cs_circulant_apply_static": [i64, vp, vp, vp, ci, vp],
         "cs_grad": [vp, vp, f32, f32, ci, ci, vp, vp, vp, vp],
+        "cs_plan_2d": [ctypes.POINTER(vp), i64, i64, i64, vp, vp, vp],
         "cs_forward_direct": [i64, i64, vp, vp, vp, vp, vp],
         "cs_batch_plan": [ctypes.POINTER(vp), ci, vp, vp, vp, vp, vp],
         "cs_batch_destroy": [vp],
@@ -158,6 +159,19 @@ def cs_plan(n: int, m: int, rows, c, stream=None) -> Plan:
     code = _lib.cs_plan(ctypes.byref(h), n, m, rows.ctypes.data, c.ctypes.data, _stream_handle(stream))
     _check(code, "cs_plan")
     return Plan(h.value, n, m)
+
+
+def cs_plan_2d(n0: int, n1: int, m: int, pix, c2, stream=None) -> Plan:
+    """Plan of the 2D blur A = P H of an n0 x n1 image (flattened row-major);
+    pix: int64 (m,) kept pixels, c2: float64 (n0, n1) generating array."""
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    c2 = np.ascontiguousarray(c2, dtype=np.float64)
+    if pix.shape != (m,) or c2.shape != (n0, n1):
+        raise ValueError("pix must have shape (m,) and c2 shape (n0, n1)")
+    h = ctypes.c_void_p()
+    code = _lib.cs_plan_2d(ctypes.byref(h), n0, n1, m, pix.ctypes.data, c2.ctypes.data, _stream_handle(stream))
+    _check(code, "cs_plan_2d")
+    return Plan(h.value, n0 * n1, m)
 
 
 def cs_plan_destroy(plan: Plan):

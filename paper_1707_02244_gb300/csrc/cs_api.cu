@@ -105,15 +105,45 @@ void make_geo(Geo& g, int lgN) {
   g.lgU = lgUmax < lgUnits ? lgUmax : lgUnits;
   g.U = 1 << g.lgU;
   g.mid_ctas = (g.N2 >> 1) >> g.lgU;
+  g.col_tile = 4096;
+  g.twod = 0;
+}
+
+// 2D DFT of an N2 x N1 array (2^lgN2 rows of 2^lgN1): the same two passes
+// without the four-step twiddle.  Column pass: 4096-value tiles while
+// N2 <= 2048, 8192-value tiles of two columns for N2 = 4096.
+void make_geo2d(Geo& g, int lgN2, int lgN1) {
+  g.lgN = lgN2 + lgN1;
+  g.N = 1 << g.lgN;
+  g.lgN2 = lgN2;
+  g.N2 = 1 << lgN2;
+  g.lgN1 = lgN1;
+  g.N1 = 1 << lgN1;
+  const int lgCol = lgN2 <= 11 ? 12 : 13;
+  g.col_tile = 1 << lgCol;
+  g.lgG = (lgCol - lgN2) < lgN1 ? (lgCol - lgN2) : lgN1;
+  g.G = 1 << g.lgG;
+  g.col_ctas = g.N1 >> g.lgG;
+  const int lgMid = lgN1 <= 11 ? 12 : 13;
+  g.tile = 1 << lgMid;
+  int lgU = lgMid - 1 - lgN1;
+  if (lgU > lgN2 - 1) lgU = lgN2 - 1;
+  if (lgU > 5) lgU = 5;   // 2U <= 64 rows
+  g.lgU = lgU;
+  g.U = 1 << lgU;
+  g.mid_ctas = (g.N2 >> 1) >> lgU;
+  g.twod = 1;
 }
 
 // Geometry invariants the pass kernels rely on (checked for every plan).
 bool geo_ok(const Geo& g) {
+  if (g.twod)
+    return g.N2 >= 2 && g.N1 >= 2 && g.G >= 2 && g.col_ctas >= 1 && g.mid_ctas >= 1 && g.U >= 1 &&
+           2 * g.U <= 64 && (2 * g.U) * g.N1 <= g.tile && (g.G << g.lgN2) <= g.col_tile && g.N1 <= 4096 &&
+           (g.col_tile == 4096 || (g.lgN2 == 12 && g.lgG == 1));
   return g.N1 >= g.N2 && g.N2 >= 2 && g.G >= 2 && g.col_ctas >= 1 && g.mid_ctas >= 1 &&
          2 * g.U <= 64 && (2 * g.U) * g.N1 <= g.tile && (g.G << g.lgN2) <= 4096;
 }
-
-int64_t tab_count(const Geo& g) { return ((int64_t)(g.N2 >> 1) << g.lgN1) + 1; }
 
 cs_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return CS_OK;
@@ -335,6 +365,11 @@ bool valid_ptr(const void* q) { return q != nullptr && ((uintptr_t)q & 7u) == 0;
 
 }  // namespace
 
+namespace {
+cs_status build_plan(cs_plan_t* out, int64_t n0, int64_t n1, int64_t m, const int64_t* rows, const double* c,
+                     void* stream);
+}  // namespace
+
 extern "C" {
 
 int cs_version(void) { return 100; }
@@ -357,6 +392,30 @@ cs_status cs_plan(cs_plan_t* out, int64_t n, int64_t m, const int64_t* rows, con
   *out = nullptr;
   if (m < 1 || m > n) return CS_ERR_ARG;
   if (n < 64 || n > (int64_t(1) << 22) || (n & (n - 1)) != 0) return CS_ERR_UNSUPPORTED;
+  return build_plan(out, 0, n, m, rows, c, stream);
+}
+
+cs_status cs_plan_2d(cs_plan_t* out, int64_t n0, int64_t n1, int64_t m, const int64_t* pix, const double* c2,
+                     void* stream) {
+  if (!out || !pix || !c2) return CS_ERR_ARG;
+  *out = nullptr;
+  if (n0 < 8 || n1 < 16 || n0 > 4096 || n1 > 4096 || (n0 & (n0 - 1)) != 0 || (n1 & (n1 - 1)) != 0)
+    return CS_ERR_UNSUPPORTED;
+  if (m < 1 || m > n0 * n1) return CS_ERR_ARG;
+  return build_plan(out, n0, n1, m, pix, c2, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Plan of the 1D operator (n0 = 0, n = n1) or of the 2D blur of an n0 x n1
+// image (flattened row-major, n = n0 n1): geometry, FP64 spectrum, tables,
+// row masks.
+cs_status build_plan(cs_plan_t* out, int64_t n0, int64_t n1, int64_t m, const int64_t* rows, const double* c,
+                     void* stream) {
+  const bool twod = n0 > 0;
+  const int64_t n = twod ? n0 * n1 : n1;
   cs_plan_s* p = new (std::nothrow) cs_plan_s();
   if (!p) return CS_ERR_NOMEM;
   p->n = n;
@@ -365,8 +424,13 @@ cs_status cs_plan(cs_plan_t* out, int64_t n, int64_t m, const int64_t* rows, con
   const char* env = std::getenv("CS_GRAPHS");
   p->use_graphs = !(env && env[0] == '0');
   const int lgn = ilog2(n);
-  make_geo(p->gi, lgn - 1);
-  make_geo(p->ga, lgn);
+  if (twod) {
+    make_geo2d(p->gi, ilog2(n0), ilog2(n1) - 1);
+    make_geo2d(p->ga, ilog2(n0), ilog2(n1));
+  } else {
+    make_geo(p->gi, lgn - 1);
+    make_geo(p->ga, lgn);
+  }
   if (!geo_ok(p->gi) || !geo_ok(p->ga)) {
     delete p;
     return CS_ERR_UNSUPPORTED;
@@ -439,9 +503,15 @@ cs_status cs_plan(cs_plan_t* out, int64_t n, int64_t m, const int64_t* rows, con
   CS_PLAN_TRY(make_tables(p->gi, p->twi, s));
   CS_PLAN_TRY(make_tables(p->ga, p->twa, s));
   double2* chat = nullptr;
-  CS_PLAN_TRY(launch_fft64(d_c, fa, fb, n, &chat, s));
-  CS_PLAN_TRY(launch_tab_ista(chat, p->gi, n, p->tab_ista, p->tab_ista_b, s));
-  CS_PLAN_TRY(launch_tab_admm(chat, p->ga, n, p->tab_admm_c, p->abs2, s));
+  if (twod) {
+    CS_PLAN_TRY(launch_fft64_2d(d_c, fa, fb, n0, n1, &chat, s));
+    CS_PLAN_TRY(launch_tab_ista2d(chat, p->gi, n0, n1, p->tab_ista, p->tab_ista_b, s));
+    CS_PLAN_TRY(launch_tab_admm2d(chat, p->ga, n0, n1, p->tab_admm_c, p->abs2, s));
+  } else {
+    CS_PLAN_TRY(launch_fft64(d_c, fa, fb, n, &chat, s));
+    CS_PLAN_TRY(launch_tab_ista(chat, p->gi, n, p->tab_ista, p->tab_ista_b, s));
+    CS_PLAN_TRY(launch_tab_admm(chat, p->ga, n, p->tab_admm_c, p->abs2, s));
+  }
   CS_PLAN_TRY(launch_tab_admm_b(p->abs2, (int)tab_count(p->ga), n, 1.0, 1.0, p->tab_admm_b, s));
   p->b_rho = 1.0;
   p->b_sigma = 1.0;
@@ -464,6 +534,10 @@ cs_status cs_plan(cs_plan_t* out, int64_t n, int64_t m, const int64_t* rows, con
   *out = p;
   return CS_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 cs_status cs_plan_destroy(cs_plan_t plan) {
   if (!plan) return CS_ERR_ARG;
@@ -834,6 +908,7 @@ cs_status cs_grad(cs_plan_t p, const float* y, float lambda, float tau, int T, i
   if (!p || !y || !valid_ptr(gx_T) || !valid_ptr(dc) || !dlambda || !dy || T < 1 || K < 1 || K > T ||
       !(lambda >= 0.f) || !(tau > 0.f) || !std::isfinite(lambda) || !std::isfinite(tau))
     return CS_ERR_ARG;
+  if (p->gi.twod) return CS_ERR_UNSUPPORTED;
   cudaStream_t s = p->stream;
   const int S = (T + K - 1) / K;   // segments; segment s covers steps [sK, min((s+1)K, T))
   CS_TRY(grad_reserve(p, S, K));

@@ -81,6 +81,26 @@ __global__ void fft64_stage_k(const double2* __restrict__ in, double2* __restric
   out[o + Ls] = make_double2(a.x - b.x, a.y - b.y);
 }
 
+// The same stage over `batch` transforms of length L with element i of
+// transform t at t * bs + i * es (rows: es = 1, bs = L; columns: es = width,
+// bs = 1).
+__global__ void fft64_strided_stage_k(const double2* __restrict__ in, double2* __restrict__ out, int64_t L,
+                                      int64_t Ls, int64_t batch, int64_t es, int64_t bs) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t h = L >> 1;
+  if (idx >= h * batch) return;
+  const int64_t t = idx / h, j = idx - t * h;
+  const int64_t k = j & (Ls - 1);
+  double s, c;
+  sincospi(-(double)k / (double)Ls, &s, &c);
+  const int64_t base = t * bs;
+  const double2 a = in[base + j * es], b0 = in[base + (j + h) * es];
+  const double2 b = make_double2(b0.x * c - b0.y * s, b0.x * s + b0.y * c);
+  const int64_t o = ((j - k) << 1) + k;
+  out[base + o * es] = make_double2(a.x + b.x, a.y + b.y);
+  out[base + (o + Ls) * es] = make_double2(a.x - b.x, a.y - b.y);
+}
+
 // chat_k of a real vector: bins 0 and n/2 are real by construction.
 __device__ __forceinline__ double2 chat_at(const double2* chat, int64_t n, int64_t k) {
   double2 v = chat[k];
@@ -117,6 +137,58 @@ __global__ void tab_ista_k(const double2* __restrict__ chat, Geo g, int64_t n, f
   tabA[t] = make_float4((float)(Px - Qx * sn), (float)(Py - Qy * sn), (float)(Px + Qx * sn),
                         (float)(-(Py + Qy * sn)));
   tabB[t] = make_float2((float)(-Qy * cs), (float)(Qx * cs));
+}
+
+// 2D: bins (k0, k1) with k0 in {0, n0/2} and k1 in {0, n1/2} are real.
+__device__ __forceinline__ double2 chat2_at(const double2* chat2, int64_t n0, int64_t n1, int64_t k0, int64_t k1) {
+  double2 v = chat2[k0 * n1 + k1];
+  if ((k0 == 0 || k0 == (n0 >> 1)) && (k1 == 0 || k1 == (n1 >> 1))) v.y = 0.0;
+  return v;
+}
+
+// 2D frequency (k2, k1) of pair slot t: rows (u, N2 - u) for units u >= 1;
+// unit 0 holds rows 0 and N2/2, each with N1/2 + 1 slots (columns q and
+// (N1 - q) mod N1).
+__device__ __forceinline__ void slot_freq2d(const Geo& g, int64_t t, int64_t& k2, int64_t& k1) {
+  const int64_t units1 = (int64_t)((g.N2 >> 1) - 1) << g.lgN1;
+  if (t < units1) {
+    k2 = (t >> g.lgN1) + 1;
+    k1 = t & (g.N1 - 1);
+    return;
+  }
+  const int64_t q = t - units1;
+  if (q <= (g.N1 >> 1)) { k2 = 0; k1 = q; }
+  else { k2 = g.N2 >> 1; k1 = q - (g.N1 >> 1) - 1; }
+}
+
+// Packed real 2D geometry (N2 = n0 rows, N1 = n1/2 packed columns): as
+// tab_ista_k with H_k -> chat2[k2, k1], H_{k+N} -> chat2[k2, k1 + N1] and the
+// packing phase exp(-2 pi i k1 / n1).
+__global__ void tab_ista2d_k(const double2* __restrict__ chat2, Geo g, int64_t n0, int64_t n1,
+                             float4* __restrict__ tabA, float2* __restrict__ tabB, int64_t count) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int64_t k2, k1;
+  slot_freq2d(g, t, k2, k1);
+  const double2 a = chat2_at(chat2, n0, n1, k2, k1), b = chat2_at(chat2, n0, n1, k2, k1 + g.N1);
+  const double s = 0.5 / (double)g.N;
+  const double Px = (a.x + b.x) * s, Py = (a.y + b.y) * s, Qx = (a.x - b.x) * s, Qy = (a.y - b.y) * s;
+  double sn, cs;
+  sincospi((double)k1 / (double)g.N1, &sn, &cs);
+  tabA[t] = make_float4((float)(Px - Qx * sn), (float)(Py - Qy * sn), (float)(Px + Qx * sn),
+                        (float)(-(Py + Qy * sn)));
+  tabB[t] = make_float2((float)(-Qy * cs), (float)(Qx * cs));
+}
+
+__global__ void tab_admm2d_k(const double2* __restrict__ chat2, Geo g, int64_t n0, int64_t n1,
+                             float2* __restrict__ tabc, double* __restrict__ abs2, int64_t count) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int64_t k2, k1;
+  slot_freq2d(g, t, k2, k1);
+  const double2 a = chat2_at(chat2, n0, n1, k2, k1);
+  tabc[t] = make_float2((float)a.x, (float)a.y);
+  abs2[t] = a.x * a.x + a.y * a.y;
 }
 
 // Complex-n geometry (N = n): chat_k in fp32 and |chat_k|^2 in FP64.
@@ -319,6 +391,38 @@ cudaError_t launch_fft64(const double* c, double2* a, double2* b, int64_t n, dou
   return cudaGetLastError();
 }
 
+cudaError_t launch_fft64_2d(const double* c2, double2* a, double2* b, int64_t n0, int64_t n1, double2** out,
+                            cudaStream_t s) {
+  const int64_t n = n0 * n1;
+  c_to_complex_k<<<blocks_for(n), AUX_NT, 0, s>>>(c2, a, n);
+  double2* in = a;
+  double2* o = b;
+  for (int64_t Ls = 1; Ls < n1; Ls <<= 1) {   // rows
+    fft64_strided_stage_k<<<blocks_for(n >> 1), AUX_NT, 0, s>>>(in, o, n1, Ls, n0, 1, n1);
+    double2* t = in; in = o; o = t;
+  }
+  for (int64_t Ls = 1; Ls < n0; Ls <<= 1) {   // columns
+    fft64_strided_stage_k<<<blocks_for(n >> 1), AUX_NT, 0, s>>>(in, o, n0, Ls, n1, n1, 1);
+    double2* t = in; in = o; o = t;
+  }
+  *out = in;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tab_ista2d(const double2* chat2, const Geo& g, int64_t n0, int64_t n1, float4* tabA,
+                              float2* tabB, cudaStream_t s) {
+  const int64_t cnt = tab_count(g);
+  tab_ista2d_k<<<blocks_for(cnt), AUX_NT, 0, s>>>(chat2, g, n0, n1, tabA, tabB, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tab_admm2d(const double2* chat2, const Geo& g, int64_t n0, int64_t n1, float2* tabc,
+                              double* abs2, cudaStream_t s) {
+  const int64_t cnt = tab_count(g);
+  tab_admm2d_k<<<blocks_for(cnt), AUX_NT, 0, s>>>(chat2, g, n0, n1, tabc, abs2, cnt);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fft64_complex(double2* a, double2* b, int64_t n, double2** out, cudaStream_t s) {
   double2* in = a;
   double2* o = b;
@@ -330,7 +434,6 @@ cudaError_t launch_fft64_complex(double2* a, double2* b, int64_t n, double2** ou
   return cudaGetLastError();
 }
 
-static int64_t tab_count(const Geo& g) { return ((int64_t)(g.N2 >> 1) << g.lgN1) + 1; }
 
 cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tabA, float2* tabB,
                             cudaStream_t s) {

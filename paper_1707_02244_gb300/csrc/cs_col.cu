@@ -10,10 +10,13 @@ namespace {
 
 // ---------------------------------------------------------------- column pass
 
-// The column pass always uses 4096-value tiles (N2 <= 1024 gives G >= 4
-// columns), 4 CTAs per SM.
+// The column pass uses 4096-value tiles (4 CTAs per SM; 1D: N2 <= 1024
+// gives G >= 4 columns), and 8192-value tiles of two 4096-long columns for
+// 2D arrays of 4096 rows (2 CTAs per SM).
 constexpr int COL_TILE = 4096;
 constexpr int COL_MINB = 4;
+constexpr int COL_TILE2 = 8192;
+constexpr int COL_MINB2 = 2;
 
 // Epilogue as the post hook of the inverse column FFT: runs on each value as
 // the last stage produces it, so the elementwise step costs no extra pass
@@ -50,10 +53,23 @@ template <> struct ColShape<1> {
   __device__ static constexpr int lgG(const Geo&) { return 2; }
   __device__ static constexpr int lgN2(const Geo&) { return 10; }
 };
+// SHAPE 2: N2 = 4096 and G = 2 (2D arrays of 4096 rows), 8192-value tiles.
+template <> struct ColShape<2> {
+  using Lay = StaticLayout<12, 1, true>;
+  __device__ static Lay lay(const Geo&) { return Lay{}; }
+  __device__ static constexpr int lgG(const Geo&) { return 1; }
+  __device__ static constexpr int lgN2(const Geo&) { return 12; }
+};
+
+template <int SHAPE> struct ColTile {
+  static constexpr int kTile = SHAPE == 2 ? COL_TILE2 : COL_TILE;
+  static constexpr int kMinB = SHAPE == 2 ? COL_MINB2 : COL_MINB;
+  static constexpr int kLgN2 = SHAPE == 2 ? 12 : 10;   // static shapes
+};
 
 template <int KIND, int SHAPE>
-__global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB) col_kernel(const KParams kp) {
-  constexpr int TILE = COL_TILE;
+__global__ void __launch_bounds__(ColTile<SHAPE>::kTile / EPT, ColTile<SHAPE>::kMinB) col_kernel(const KParams kp) {
+  constexpr int TILE = ColTile<SHAPE>::kTile;
   constexpr int NT = Cfg<TILE>::NT;
   constexpr int NLD = Cfg<TILE>::NLD;
   using E = Epi<KIND>;
@@ -67,7 +83,7 @@ __global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB) col_kernel(const KPa
   const int tot = G << lgN2;
   const auto lay = S::lay(g);
   constexpr bool TWS = SHAPE != 0;   // static shape: stage-major twiddles in shared memory
-  constexpr int TW_N = TWS ? stage_tw_count(10) : 2;
+  constexpr int TW_N = TWS ? stage_tw_count(ColTile<SHAPE>::kLgN2) : 2;
   __shared__ __align__(16) float2 tws[TW_N];
   const float2* tw = TWS ? tws : g.tw2;
   if (TWS) copy_table<NT>(tws, g.tws2, TW_N);   // plan constant
@@ -168,6 +184,12 @@ __global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB) col_kernel(const KPa
 
 }  // namespace
 
+// kinds of the 2D solves (no gradient)
+#define CS_COL_KINDS_2D(X, S)                                                                  \
+  X(COL_LOAD, S) X(COL_LOAD_SCALED, S) X(COL_STORE, S) X(COL_MASK, S) X(COL_RESIDUAL, S)         \
+  X(COL_ISTA, S) X(COL_ISTA_LAST, S) X(COL_POWER_OUT, S) X(COL_ADMM_INIT, S) X(COL_ADMM, S)       \
+  X(COL_ADMM_LAST, S)
+
 #define CS_COL_KINDS(X, S)                                                                     \
   X(COL_LOAD, S) X(COL_LOAD_SCALED, S) X(COL_STORE, S) X(COL_MASK, S) X(COL_RESIDUAL, S)         \
   X(COL_ISTA, S) X(COL_ISTA_LAST, S) X(COL_POWER_OUT, S) X(COL_ADMM_INIT, S) X(COL_ADMM, S)       \
@@ -176,9 +198,11 @@ __global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB) col_kernel(const KPa
 
 cudaError_t init_col_kernels() {
   cudaError_t e = cudaSuccess;
-#define CS_SET_COL(k, S) if (e == cudaSuccess) e = set_smem(col_kernel<k, S>, COL_TILE, COL_MINB);
+#define CS_SET_COL(k, S) \
+  if (e == cudaSuccess) e = set_smem(col_kernel<k, S>, ColTile<S>::kTile, ColTile<S>::kMinB);
   CS_COL_KINDS(CS_SET_COL, 0)
   CS_COL_KINDS(CS_SET_COL, 1)
+  CS_COL_KINDS_2D(CS_SET_COL, 2)
 #undef CS_SET_COL
   return e;
 }
@@ -187,8 +211,12 @@ cudaError_t launch_col(ColKind kind, const KParams& kp, cudaStream_t s) {
   const Geo& g = kp.geo;
   const int grid = g.col_ctas;
   const bool hot = g.lgN2 == 10 && g.lgG == 2;
-#define CS_L_COL(k, S) case k: return launch_k(col_kernel<k, S>, grid, COL_TILE, kp, s);
-  if (hot) {
+#define CS_L_COL(k, S) case k: return launch_k(col_kernel<k, S>, grid, ColTile<S>::kTile, kp, s);
+  if (g.col_tile == COL_TILE2) {
+    if (g.lgN2 == 12 && g.lgG == 1) {
+      switch (kind) { CS_COL_KINDS_2D(CS_L_COL, 2) default: break; }
+    }
+  } else if (hot) {
     switch (kind) { CS_COL_KINDS(CS_L_COL, 1) }
   } else {
     switch (kind) { CS_COL_KINDS(CS_L_COL, 0) }

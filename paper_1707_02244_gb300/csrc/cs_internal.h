@@ -18,6 +18,8 @@ struct Geo {
   int G, lgG, col_ctas;
   int U, lgU, mid_ctas;
   int tile;            // mid pass: complex values per CTA (4096 or 8192); threads = tile / 16
+  int col_tile;        // column pass: complex values per CTA (4096, or 8192 for N2 = 4096)
+  int twod;            // 1: 2D DFT of the N2 x N1 array (no four-step twiddle; pairs (k2, k1) ~ (-k2, -k1))
   const float2* tw1;   // exp(-2 pi i q / (2 N1)), q < 2 N1
   const float2* tw2;   // exp(-2 pi i q / N2),     q < N2
   const float2* twl;   // exp(-2 pi i q / N),      q < N1
@@ -132,6 +134,17 @@ cudaError_t launch_fft64(const double* c, double2* a, double2* b, int64_t n, dou
 cudaError_t launch_fft64_complex(double2* a, double2* b, int64_t n, double2** out, cudaStream_t s);
 cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tabA, float2* tabB,
                             cudaStream_t s);
+// 2D: chat2 is the n0 x n1 FP64 spectrum (row-major); g the 2D geometry.
+cudaError_t launch_tab_ista2d(const double2* chat2, const Geo& g, int64_t n0, int64_t n1, float4* tabA,
+                              float2* tabB, cudaStream_t s);
+cudaError_t launch_tab_admm2d(const double2* chat2, const Geo& g, int64_t n0, int64_t n1, float2* tabc,
+                              double* abs2, cudaStream_t s);
+// FP64 2D DFT of the real n0 x n1 array c2 (row-major); a, b work space of
+// n0 n1 values each; *out is whichever holds the result.
+cudaError_t launch_fft64_2d(const double* c2, double2* a, double2* b, int64_t n0, int64_t n1, double2** out,
+                            cudaStream_t s);
+// Pair slots of the mid pass (spectrum tables' length).
+inline int64_t tab_count(const Geo& g) { return ((int64_t)(g.N2 >> 1) << g.lgN1) + (g.twod ? 2 : 1); }
 cudaError_t launch_stage_tw(float2* dst, int lgL, int count, cudaStream_t s);
 cudaError_t launch_tab_admm(const double2* chat, const Geo& g, int64_t n, float2* tabc,
                             double* abs2, cudaStream_t s);

@@ -114,15 +114,20 @@ __device__ __forceinline__ void op_admm(const PlanPtrs& pp, float rho, float sig
 // SHAPE 0: any geometry; SHAPE s > 0 fixes (log2 N1, log2 U) at compile time
 // for the geometries of N = 2^20 (1024 x 1024, U = 2), 2^21 (2048 x 1024,
 // U = 1) and 2^22 (4096 x 1024, U = 1).
+// SHAPE 4..6: the same for a 2D DFT (no four-step twiddle; see Geo::twod):
+// 4 any geometry, 5 and 6 fix (log2 N1, log2 U) = (11, 0) and (12, 0), the
+// packed and the complex geometry of a 4096 x 4096 image.
 template <int SHAPE> struct MidShape;
 template <> struct MidShape<0> {
   using Lay = DynLayout;
+  static constexpr bool kTwoD = false;
   __device__ static Lay lay(const Geo& g) { return Lay{g.lgN1, g.lgU + 1, false}; }
   __device__ static int lgN1(const Geo& g) { return g.lgN1; }
   __device__ static int lgU(const Geo& g) { return g.lgU; }
 };
-template <int LGN1, int LGU> struct MidShapeS {
+template <int LGN1, int LGU, bool TWOD = false> struct MidShapeS {
   using Lay = StaticLayout<LGN1, LGU + 1, false>;
+  static constexpr bool kTwoD = TWOD;
   __device__ static Lay lay(const Geo&) { return Lay{}; }
   __device__ static constexpr int lgN1(const Geo&) { return LGN1; }
   __device__ static constexpr int lgU(const Geo&) { return LGU; }
@@ -130,6 +135,9 @@ template <int LGN1, int LGU> struct MidShapeS {
 template <> struct MidShape<1> : MidShapeS<10, 1> {};
 template <> struct MidShape<2> : MidShapeS<11, 0> {};
 template <> struct MidShape<3> : MidShapeS<12, 0> {};
+template <> struct MidShape<4> : MidShape<0> { static constexpr bool kTwoD = true; };
+template <> struct MidShape<5> : MidShapeS<11, 0, true> {};
+template <> struct MidShape<6> : MidShapeS<12, 0, true> {};
 
 template <int KIND, int TILE, int SHAPE>
 __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(const KParams kp) {
@@ -145,17 +153,19 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
   const int tot = (2 * U) << lgN1;
   const auto lay = S::lay(g);
   float2* __restrict__ W = kp.pp.W;
-  constexpr bool TWS = SHAPE != 0;   // static shape: twiddles in shared memory
-  constexpr int LGN1S = SHAPE == 0 ? 4 : S::lgN1(Geo{});
-  constexpr int ROWS = SHAPE == 0 ? MID_MAX_ROWS : (2 << S::lgU(Geo{}));
-  constexpr int TW_N = SHAPE == 0 ? 2 : stage_tw_count(LGN1S);
+  constexpr bool TWS = S::Lay::kStatic;   // static shape: twiddles in shared memory
+  constexpr bool TWOD = S::kTwoD;         // 2D DFT: no four-step twiddle hooks
+  constexpr int LGN1S = TWS ? S::lgN1(Geo{}) : 4;
+  constexpr int ROWS = TWS ? (2 << S::lgU(Geo{})) : MID_MAX_ROWS;
+  constexpr int TW_N = TWS ? stage_tw_count(LGN1S) : 2;
   __shared__ __align__(16) float2 tws[TW_N];
   // static shapes: per-row lo[16] and hi[N1/16]; dynamic: rt (see MidTwHook)
-  constexpr int LOHI = SHAPE == 0 ? 2 : ROWS * (16 + (1 << (LGN1S - 4)));
+  constexpr int LOHI = (TWS && !TWOD) ? ROWS * (16 + (1 << (LGN1S - 4))) : 2;
   __shared__ float2 lohi[LOHI];
-  __shared__ float2 rt[2][SHAPE == 0 ? MID_MAX_ROWS * 16 : 2];
-  if (TWS) {
-    copy_table<NT>(tws, g.tws1, TW_N);
+  __shared__ float2 rt[2][(TWS || TWOD) ? 2 : MID_MAX_ROWS * 16];
+  if (TWS) copy_table<NT>(tws, g.tws1, TW_N);
+  if constexpr (TWOD) {
+  } else if (TWS) {
     constexpr int HI = 1 << (LGN1S - 4);
     for (int t = threadIdx.x; t < ROWS * (16 + HI); t += NT) {
       const bool is_lo = t < ROWS * 16;
@@ -203,7 +213,10 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
     __syncthreads();
   };
   auto fwd_rows = [&](float2* buf) {
-    if constexpr (TWS) {
+    if constexpr (TWOD) {
+      if constexpr (TWS) tile_fft<-1, TILE, NT, true>(buf, lay, tws, lgN1);
+      else tile_fft<-1, TILE, NT, false>(buf, lay, g.tw1h, lgN1);
+    } else if constexpr (TWS) {
       MidTwHookS<true> h{lohi, lohi + ROWS * 16, LGN1S, make_float2(1.f, 0.f)};
       tile_fft<-1, TILE, NT, true>(buf, lay, tws, lgN1, h);
     } else {
@@ -213,13 +226,31 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
   };
   // Pair slot t of this CTA: elements ea (frequency k = k2 + N2 k1) and eb
   // (frequency N - k) of the tile, table index tidx.
-  const int nslots = (U << lgN1) + (u0 == 0 ? 1 : 0);
+  const int nslots = (U << lgN1) + (u0 == 0 ? (TWOD ? 2 : 1) : 0);
   const int base_u1 = ((g.N2 >> 1) - 1) << lgN1;   // table offset of unit 0
   auto slot_at = [&](int t, int& ea, int& eb, int& k2, int& k1, int& tidx) {
     int ul, q;
     if (t < (U << lgN1)) { ul = t >> lgN1; q = t & (N1 - 1); }
-    else { ul = 0; q = N1; }
+    else { ul = 0; q = N1 + (t - (U << lgN1)); }
     const int u = u0 + ul;
+    if constexpr (TWOD) {
+      // 2D partner of (k2, k1): (-k2, -k1); unit 0: rows 0 and N2/2, each
+      // with N1/2 + 1 slots q -> (q, (N1 - q) mod N1)
+      if (u > 0) {
+        k2 = u; k1 = q;
+        ea = ((2 * ul) << lgN1) + q;
+        eb = ((2 * ul + 1) << lgN1) + ((N1 - q) & (N1 - 1));
+        tidx = ((u - 1) << lgN1) + q;
+      } else {
+        const bool hi = q > (N1 >> 1);
+        const int qq = hi ? q - (N1 >> 1) - 1 : q;
+        k2 = hi ? (g.N2 >> 1) : 0; k1 = qq;
+        ea = ((2 * ul + (hi ? 1 : 0)) << lgN1) + qq;
+        eb = ((2 * ul + (hi ? 1 : 0)) << lgN1) + ((N1 - qq) & (N1 - 1));
+        tidx = base_u1 + q;
+      }
+      return;
+    }
     if (u > 0) {
       k2 = u; k1 = q;
       ea = ((2 * ul) << lgN1) + q;
@@ -310,7 +341,10 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
     }
     __syncthreads();
   }
-  if constexpr (TWS) {
+  if constexpr (TWOD) {
+    if constexpr (TWS) tile_fft<+1, TILE, NT, true>(sm, lay, tws, lgN1);
+    else tile_fft<+1, TILE, NT, false>(sm, lay, g.tw1h, lgN1);
+  } else if constexpr (TWS) {
     MidTwHookS<false> h{lohi, lohi + ROWS * 16, LGN1S, make_float2(1.f, 0.f)};
     tile_fft<+1, TILE, NT, true>(sm, lay, tws, lgN1, h);
   } else {
@@ -334,6 +368,7 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
 
 #define CS_MID_KINDS(X, T, S) \
   X(MID_FWD, T, S) X(MID_ADJ, T, S) X(MID_ADMM, T, S) X(MID_CORR, T, S) X(MID_FROM_ACC, T, S)
+#define CS_MID_KINDS_2D(X, T, S) X(MID_FWD, T, S) X(MID_ADJ, T, S) X(MID_ADMM, T, S)
 
 // MID_CORR holds two tiles in shared memory
 constexpr int mid_smem_mult(int kind) { return kind == MID_CORR ? 2 : 1; }
@@ -347,6 +382,10 @@ cudaError_t init_mid_kernels() {
   CS_MID_KINDS(CS_SET_MID, 4096, 1)
   CS_MID_KINDS(CS_SET_MID, 4096, 2)
   CS_MID_KINDS(CS_SET_MID, 8192, 3)
+  CS_MID_KINDS_2D(CS_SET_MID, 4096, 4)
+  CS_MID_KINDS_2D(CS_SET_MID, 8192, 4)
+  CS_MID_KINDS_2D(CS_SET_MID, 4096, 5)
+  CS_MID_KINDS_2D(CS_SET_MID, 8192, 6)
 #undef CS_SET_MID
   return e;
 }
@@ -354,11 +393,23 @@ cudaError_t init_mid_kernels() {
 cudaError_t launch_mid(MidKind kind, const KParams& kp, cudaStream_t s) {
   const Geo& g = kp.geo;
   const int grid = g.mid_ctas;
+#define CS_L_MID(k, T, S) case k: return launch_k(mid_kernel<k, T, S>, grid, T, kp, s, mid_smem_mult(k));
+  if (g.twod) {
+    if (g.lgN1 == 11 && g.lgU == 0 && g.tile == 4096) {
+      switch (kind) { CS_MID_KINDS_2D(CS_L_MID, 4096, 5) default: break; }
+    } else if (g.lgN1 == 12 && g.lgU == 0 && g.tile == 8192) {
+      switch (kind) { CS_MID_KINDS_2D(CS_L_MID, 8192, 6) default: break; }
+    } else if (g.tile == 4096) {
+      switch (kind) { CS_MID_KINDS_2D(CS_L_MID, 4096, 4) default: break; }
+    } else {
+      switch (kind) { CS_MID_KINDS_2D(CS_L_MID, 8192, 4) default: break; }
+    }
+    return cudaErrorInvalidValue;
+  }
   int shape = 0;
   if (g.lgN1 == 10 && g.lgU == 1 && g.tile == 4096) shape = 1;
   if (g.lgN1 == 11 && g.lgU == 0 && g.tile == 4096) shape = 2;
   if (g.lgN1 == 12 && g.lgU == 0 && g.tile == 8192) shape = 3;
-#define CS_L_MID(k, T, S) case k: return launch_k(mid_kernel<k, T, S>, grid, T, kp, s, mid_smem_mult(k));
   switch (shape) {
     case 1: switch (kind) { CS_MID_KINDS(CS_L_MID, 4096, 1) } break;
     case 2: switch (kind) { CS_MID_KINDS(CS_L_MID, 4096, 2) } break;

@@ -114,3 +114,16 @@ def test_direct_product_rejects_bad_arguments_without_device(cs):
     assert cs.raw_call("cs_forward_direct", 0, 1, buf, buf, buf, buf, None) == cs.CS_ERR_ARG
     assert cs.raw_call("cs_forward_direct", 16, 17, buf, buf, buf, buf, None) == cs.CS_ERR_ARG
     assert cs.raw_call("cs_forward_direct", 16, 4, None, buf, buf, buf, None) == cs.CS_ERR_ARG
+
+
+def test_plan_2d_rejects_bad_arguments_without_device(cs):
+    h = ctypes.c_void_p()
+    pix = np.arange(8, dtype=np.int64)
+    c2 = np.zeros(8 * 16)
+    assert cs.raw_call("cs_plan_2d", None, 8, 16, 8, pix.ctypes.data, c2.ctypes.data, None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_plan_2d", ctypes.byref(h), 8, 16, 8, None, c2.ctypes.data, None) == cs.CS_ERR_ARG
+    assert cs.raw_call("cs_plan_2d", ctypes.byref(h), 8, 16, 0, pix.ctypes.data, c2.ctypes.data,
+                       None) == cs.CS_ERR_ARG
+    for n0, n1 in ((8, 8), (4, 16), (8192, 16), (12, 16), (8, 24)):
+        assert cs.raw_call("cs_plan_2d", ctypes.byref(h), n0, n1, 8, pix.ctypes.data, c2.ctypes.data,
+                           None) == cs.CS_ERR_UNSUPPORTED, (n0, n1)

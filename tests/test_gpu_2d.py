@@ -1,0 +1,131 @@
+"""GPU parity of the 2D operator (compressed deblurring: A = P H, H the
+periodic blur of an n0 x n1 image) and of ISTA / ADMM on it, against the FP64
+oracle.  The shapes cover every geometry of the 2D passes: tiny arrays (one
+CTA per pass), non-square images, 2048-row images (4096-value column tiles of
+two columns) and 4096 x 4096 (8192-value column tiles, static mid shapes).
+"""
+import numpy as np
+import pytest
+
+import oracle.cs_oracle as O
+import synth
+from gpu_util import f32, host, rel_l2, to_dev, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+REL = 2e-6
+ITER_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def cs():
+    import paper_1707_02244_gb300 as cs
+    return cs
+
+
+def _random_2d(n0, n1, m, seed, psf=False):
+    g = synth.rng(seed)
+    if psf:
+        c2 = synth.psf_generator(synth.gaussian_psf(2.5), n0, n1)
+    else:
+        c2 = g.standard_normal((n0, n1)) / np.sqrt(n0 * n1)
+    pix = synth.draw_rows(g, n0 * n1, m)
+    return c2, pix, g
+
+
+@pytest.mark.parametrize("n0,n1", [(8, 16), (32, 64), (64, 32), (16, 4096), (256, 512), (2048, 256),
+                                   (1024, 1024), (4096, 4096)])
+def test_2d_products_match_oracle(cs, n0, n1):
+    torch, dev = torch_dev()
+    n = n0 * n1
+    m = max(1, n // 3)
+    c2, pix, g = _random_2d(n0, n1, m, 9300 + n0 + n1, psf=(n0 >= 1024))
+    x = g.standard_normal(n).astype(np.float32)
+    r = g.standard_normal(m).astype(np.float32)
+    plan = cs.cs_plan_2d(n0, n1, m, pix, c2, torch.cuda.current_stream(dev))
+    try:
+        y = torch.empty(m, dtype=torch.float32, device=dev)
+        xa = torch.empty(n, dtype=torch.float32, device=dev)
+        cs.cs_forward(plan, to_dev(x), y)
+        cs.cs_adjoint(plan, to_dev(r), xa)
+        torch.cuda.synchronize()
+        yg, ag = host(y), host(xa)
+    finally:
+        plan.close()
+    if n <= 4096:
+        A = O.sensing2d_matrix(c2, pix)
+        want_y, want_a = A @ x.astype(np.float64), A.T @ r.astype(np.float64)
+    else:
+        ch = O.spectrum2d(c2)
+        want_y = O.forward2d_fft(ch, pix, x.astype(np.float64))
+        want_a = O.adjoint2d_fft(ch, pix, r.astype(np.float64))
+    assert rel_l2(yg, want_y) <= REL, rel_l2(yg, want_y)
+    assert rel_l2(ag, want_a) <= REL, rel_l2(ag, want_a)
+
+
+@pytest.mark.parametrize("n0,n1,dense", [(16, 32, True), (128, 256, False), (1024, 512, False)])
+def test_2d_ista_admm_match_oracle(cs, n0, n1, dense):
+    torch, dev = torch_dev()
+    n = n0 * n1
+    img = synth.star_field(n0, n1, k=max(2, n // 800), seed=9400 + n)
+    ch = O.spectrum2d(img.c2)
+    y32 = (O.forward2d_fft(ch, img.pix, img.x_true) + img.noise).astype(np.float32)
+    y64 = y32.astype(np.float64)
+    lam = f32(2e-3)
+    tau = f32(1.0 / np.max(np.abs(ch) ** 2))
+    plan = cs.cs_plan_2d(n0, n1, img.m, img.pix, img.c2, torch.cuda.current_stream(dev))
+    try:
+        x = torch.zeros(n, dtype=torch.float32, device=dev)
+        cs.cs_ista(plan, to_dev(y32), lam, tau, 100, x)
+        z = torch.zeros(n, dtype=torch.float32, device=dev)
+        cs.cs_admm(plan, to_dev(y32), lam, 1.0, 100, z)
+        torch.cuda.synchronize()
+        xg, zg = host(x), host(z)
+    finally:
+        plan.close()
+    if dense:
+        xo = O.ista_dense2d(img.c2, img.pix, y64, lam, tau, 100)
+        zo = O.admm_dense2d(img.c2, img.pix, y64, lam, 1.0, 1.0, iters=100)["z"]
+    else:
+        xo = O.ista_fft2d(img.c2, img.pix, y64, lam, tau, 100)
+        zo = O.admm_fft2d(img.c2, img.pix, y64, lam, 1.0, 1.0, iters=100)["z"]
+    assert rel_l2(xg, xo) <= ITER_TOL, ("ista", rel_l2(xg, xo))
+    assert rel_l2(zg, zo) <= ITER_TOL, ("admm", rel_l2(zg, zo))
+
+
+def test_2d_star_field_full_size(cs):
+    """The 4096 x 4096 star field (k = 20000, Gaussian PSF sigma 2.5 px, m =
+    n/3, noise 1e-3): 10 ISTA and 10 ADMM iterations against the FFT oracle."""
+    torch, dev = torch_dev()
+    img = synth.star_field()
+    n = img.n
+    ch = O.spectrum2d(img.c2)
+    y32 = (O.forward2d_fft(ch, img.pix, img.x_true) + img.noise).astype(np.float32)
+    y64 = y32.astype(np.float64)
+    lam, tau = f32(2e-4), f32(1.0)
+    plan = cs.cs_plan_2d(img.n0, img.n1, img.m, img.pix, img.c2, torch.cuda.current_stream(dev))
+    try:
+        x = torch.zeros(n, dtype=torch.float32, device=dev)
+        cs.cs_ista(plan, to_dev(y32), lam, tau, 10, x)
+        z = torch.zeros(n, dtype=torch.float32, device=dev)
+        cs.cs_admm(plan, to_dev(y32), lam, 1.0, 10, z)
+        torch.cuda.synchronize()
+        xg, zg = host(x), host(z)
+    finally:
+        plan.close()
+    xo = O.ista_fft2d(img.c2, img.pix, y64, lam, tau, 10)
+    zo = O.admm_fft2d(img.c2, img.pix, y64, lam, 1.0, 1.0, iters=10)["z"]
+    assert rel_l2(xg, xo) <= ITER_TOL, ("ista", rel_l2(xg, xo))
+    assert rel_l2(zg, zo) <= ITER_TOL, ("admm", rel_l2(zg, zo))
+
+
+def test_2d_plan_rejects_bad_shapes(cs):
+    c2 = np.zeros((8, 16))
+    pix = np.arange(10)
+    for n0, n1 in ((8, 8), (4, 16), (8192, 16), (12, 16)):
+        with pytest.raises(cs.CsError) as e:
+            cs.cs_plan_2d(n0, n1, 10, pix, np.zeros((n0, n1)))
+        assert e.value.code == cs.CS_ERR_UNSUPPORTED, (n0, n1)
+    with pytest.raises(cs.CsError) as e:
+        cs.cs_plan_2d(8, 16, 10, np.full(10, 200), c2)
+    assert e.value.code == cs.CS_ERR_ARG

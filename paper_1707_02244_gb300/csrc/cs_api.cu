@@ -38,7 +38,6 @@ struct cs_plan_s {
   int* status = nullptr;
   CallArgs* ca = nullptr;
   float4* tab_ista = nullptr;
-  float2* tab_ista_b = nullptr;
   float2* tab_admm_c = nullptr;
   float* tab_admm_b = nullptr;
   double* abs2 = nullptr;
@@ -168,7 +167,7 @@ void free_plan(cs_plan_s* p) {
   void* bufs[] = {p->W, p->si.mask, p->si.prefix, p->si.pos, p->si.ys, p->sa.mask, p->sa.prefix, p->sa.pos,
                   p->sa.ys, p->rows32, p->xi_t, p->xt_i, p->xt_a, p->av, p->az, p->amu, p->anu, p->ax,
                   p->partials, p->stats, p->status,
-                  p->ca, p->tab_ista, p->tab_ista_b, p->tab_admm_c, p->tab_admm_b, p->abs2, p->twi, p->twa,
+                  p->ca, p->tab_ista, p->tab_admm_c, p->tab_admm_b, p->abs2, p->twi, p->twa,
                   p->dense, p->dense2, p->dense3};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -195,7 +194,6 @@ KParams kparams(const cs_plan_s* p, const Geo& g, int flags) {
   k.pp.partials = p->partials;
   k.pp.stats = p->stats;
   k.pp.tab_ista = p->tab_ista;
-  k.pp.tab_ista_b = p->tab_ista_b;
   k.pp.tab_admm_c = p->tab_admm_c;
   k.pp.tab_admm_b = p->tab_admm_b;
   k.pp.status = p->status;
@@ -477,7 +475,6 @@ cs_status build_plan(cs_plan_t* out, int64_t n0, int64_t n1, int64_t m, const in
   CS_PLAN_TRY(dalloc(&p->status, 1));
   CS_PLAN_TRY(dalloc(&p->ca, 1));
   CS_PLAN_TRY(dalloc(&p->tab_ista, tab_count(p->gi)));
-  CS_PLAN_TRY(dalloc(&p->tab_ista_b, tab_count(p->gi)));
   CS_PLAN_TRY(dalloc(&p->tab_admm_c, tab_count(p->ga)));
   CS_PLAN_TRY(dalloc(&p->tab_admm_b, tab_count(p->ga)));
   CS_PLAN_TRY(dalloc(&p->abs2, tab_count(p->ga)));
@@ -505,11 +502,11 @@ cs_status build_plan(cs_plan_t* out, int64_t n0, int64_t n1, int64_t m, const in
   double2* chat = nullptr;
   if (twod) {
     CS_PLAN_TRY(launch_fft64_2d(d_c, fa, fb, n0, n1, &chat, s));
-    CS_PLAN_TRY(launch_tab_ista2d(chat, p->gi, n0, n1, p->tab_ista, p->tab_ista_b, s));
+    CS_PLAN_TRY(launch_tab_ista2d(chat, p->gi, n0, n1, p->tab_ista, s));
     CS_PLAN_TRY(launch_tab_admm2d(chat, p->ga, n0, n1, p->tab_admm_c, p->abs2, s));
   } else {
     CS_PLAN_TRY(launch_fft64(d_c, fa, fb, n, &chat, s));
-    CS_PLAN_TRY(launch_tab_ista(chat, p->gi, n, p->tab_ista, p->tab_ista_b, s));
+    CS_PLAN_TRY(launch_tab_ista(chat, p->gi, n, p->tab_ista, s));
     CS_PLAN_TRY(launch_tab_admm(chat, p->ga, n, p->tab_admm_c, p->abs2, s));
   }
   CS_PLAN_TRY(launch_tab_admm_b(p->abs2, (int)tab_count(p->ga), n, 1.0, 1.0, p->tab_admm_b, s));

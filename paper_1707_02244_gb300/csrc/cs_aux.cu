@@ -125,18 +125,14 @@ __device__ __forceinline__ int64_t slot_freq(const Geo& g, int64_t t) {
 //   a = P - Q sin(theta),  a' = conj(P + Q sin(theta)),  b = i Q cos(theta),
 // all in FP64, rounded once: tabA = (a, a'), tabB = b.
 __global__ void tab_ista_k(const double2* __restrict__ chat, Geo g, int64_t n, float4* __restrict__ tabA,
-                           float2* __restrict__ tabB, int64_t count) {
+                           int64_t count) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count) return;
   const int64_t k = slot_freq(g, t);
   const double2 a = chat_at(chat, n, k), b = chat_at(chat, n, k + g.N);
   const double s = 0.5 / (double)g.N;
-  const double Px = (a.x + b.x) * s, Py = (a.y + b.y) * s, Qx = (a.x - b.x) * s, Qy = (a.y - b.y) * s;
-  double sn, cs;
-  sincospi((double)k / (double)g.N, &sn, &cs);
-  tabA[t] = make_float4((float)(Px - Qx * sn), (float)(Py - Qy * sn), (float)(Px + Qx * sn),
-                        (float)(-(Py + Qy * sn)));
-  tabB[t] = make_float2((float)(-Qy * cs), (float)(Qx * cs));
+  tabA[t] = make_float4((float)((a.x + b.x) * s), (float)((a.y + b.y) * s), (float)((a.x - b.x) * s),
+                        (float)((a.y - b.y) * s));
 }
 
 // 2D: bins (k0, k1) with k0 in {0, n0/2} and k1 in {0, n1/2} are real.
@@ -165,19 +161,15 @@ __device__ __forceinline__ void slot_freq2d(const Geo& g, int64_t t, int64_t& k2
 // tab_ista_k with H_k -> chat2[k2, k1], H_{k+N} -> chat2[k2, k1 + N1] and the
 // packing phase exp(-2 pi i k1 / n1).
 __global__ void tab_ista2d_k(const double2* __restrict__ chat2, Geo g, int64_t n0, int64_t n1,
-                             float4* __restrict__ tabA, float2* __restrict__ tabB, int64_t count) {
+                             float4* __restrict__ tabA, int64_t count) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count) return;
   int64_t k2, k1;
   slot_freq2d(g, t, k2, k1);
   const double2 a = chat2_at(chat2, n0, n1, k2, k1), b = chat2_at(chat2, n0, n1, k2, k1 + g.N1);
   const double s = 0.5 / (double)g.N;
-  const double Px = (a.x + b.x) * s, Py = (a.y + b.y) * s, Qx = (a.x - b.x) * s, Qy = (a.y - b.y) * s;
-  double sn, cs;
-  sincospi((double)k1 / (double)g.N1, &sn, &cs);
-  tabA[t] = make_float4((float)(Px - Qx * sn), (float)(Py - Qy * sn), (float)(Px + Qx * sn),
-                        (float)(-(Py + Qy * sn)));
-  tabB[t] = make_float2((float)(-Qy * cs), (float)(Qx * cs));
+  tabA[t] = make_float4((float)((a.x + b.x) * s), (float)((a.y + b.y) * s), (float)((a.x - b.x) * s),
+                        (float)((a.y - b.y) * s));
 }
 
 __global__ void tab_admm2d_k(const double2* __restrict__ chat2, Geo g, int64_t n0, int64_t n1,
@@ -410,9 +402,9 @@ cudaError_t launch_fft64_2d(const double* c2, double2* a, double2* b, int64_t n0
 }
 
 cudaError_t launch_tab_ista2d(const double2* chat2, const Geo& g, int64_t n0, int64_t n1, float4* tabA,
-                              float2* tabB, cudaStream_t s) {
+                              cudaStream_t s) {
   const int64_t cnt = tab_count(g);
-  tab_ista2d_k<<<blocks_for(cnt), AUX_NT, 0, s>>>(chat2, g, n0, n1, tabA, tabB, cnt);
+  tab_ista2d_k<<<blocks_for(cnt), AUX_NT, 0, s>>>(chat2, g, n0, n1, tabA, cnt);
   return cudaGetLastError();
 }
 
@@ -435,10 +427,9 @@ cudaError_t launch_fft64_complex(double2* a, double2* b, int64_t n, double2** ou
 }
 
 
-cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tabA, float2* tabB,
-                            cudaStream_t s) {
+cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tabA, cudaStream_t s) {
   const int64_t cnt = tab_count(g);
-  tab_ista_k<<<blocks_for(cnt), AUX_NT, 0, s>>>(chat, g, n, tabA, tabB, cnt);
+  tab_ista_k<<<blocks_for(cnt), AUX_NT, 0, s>>>(chat, g, n, tabA, cnt);
   return cudaGetLastError();
 }
 

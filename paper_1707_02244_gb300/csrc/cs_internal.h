@@ -49,8 +49,7 @@ struct PlanPtrs {
   const float* ys;           // y in tile order of its rows, [m]
   double* partials;          // [max_ctas * NSTAT]
   double* stats;             // [NSTAT] finalised sums
-  const float4* tab_ista;    // (a, a') per pair slot, real-FFT geometry
-  const float2* tab_ista_b;  // b per pair slot
+  const float4* tab_ista;    // (P, Q) per pair slot, real-FFT geometry (see op_real)
   const float2* tab_admm_c;  // chat_k per pair slot, complex-n geometry
   const float* tab_admm_b;   // 1 / (n (rho |chat_k|^2 + sigma)) per pair slot
   int* status;               // device status word
@@ -132,11 +131,10 @@ cudaError_t launch_fft64(const double* c, double2* a, double2* b, int64_t n, dou
 // Forward FP64 FFT of the complex vector in a (b is work space); *out is
 // whichever of a / b holds the result.
 cudaError_t launch_fft64_complex(double2* a, double2* b, int64_t n, double2** out, cudaStream_t s);
-cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tabA, float2* tabB,
-                            cudaStream_t s);
+cudaError_t launch_tab_ista(const double2* chat, const Geo& g, int64_t n, float4* tabA, cudaStream_t s);
 // 2D: chat2 is the n0 x n1 FP64 spectrum (row-major); g the 2D geometry.
 cudaError_t launch_tab_ista2d(const double2* chat2, const Geo& g, int64_t n0, int64_t n1, float4* tabA,
-                              float2* tabB, cudaStream_t s);
+                              cudaStream_t s);
 cudaError_t launch_tab_admm2d(const double2* chat2, const Geo& g, int64_t n0, int64_t n1, float2* tabc,
                               double* abs2, cudaStream_t s);
 // FP64 2D DFT of the real n0 x n1 array c2 (row-major); a, b work space of

@@ -71,14 +71,21 @@ struct MidTwHook {
 // spectrum of the product (H = chat for C^T, conj(chat) for C):
 //   Z'_k   = a  Z_k   + b  conj(Z_{N-k})
 //   Z'_N-k = a' Z_N-k + b' conj(Z_k),   b' = -conj(b)
-// where (a, a', b) are tabulated for H = chat (FP64 at plan time: a = P - Q sin,
-// a' = conj(P + Q sin), b = i Q cos, P = (H_k + H_{k+N})/2N, Q = (H_k - H_{k+N})/2N,
-// angle 2 pi k / 2N).  H = conj(chat) conjugates a and a' and maps b -> -conj(b).
+// with, for H = chat, P = (H_k + H_{k+N})/2N, Q = (H_k - H_{k+N})/2N (the
+// table, FP64-rounded once) and the packing phase w = exp(-i theta),
+// theta = 2 pi k / 2N:  a = P - Q sin(theta), a' = conj(P + Q sin(theta)),
+// b = i Q cos(theta).  H = conj(chat) conjugates a and a' and maps
+// b -> -conj(b).  w = w_2N^k is the product of two small tables (1D:
+// twr[k2] tw1[k1]; 2D, where the phase is that of the packed axis only:
+// tw1[k1]).
 template <bool ADJ>
-__device__ __forceinline__ void op_real(const PlanPtrs& pp, int tidx, float2& za, float2& zb) {
+__device__ __forceinline__ void op_real(const PlanPtrs& pp, int tidx, float2 w, float2& za, float2& zb) {
   const float4 t = __ldg(pp.tab_ista + tidx);
-  float2 al = make_float2(t.x, t.y), al2 = make_float2(t.z, t.w);
-  float2 be = __ldg(pp.tab_ista_b + tidx);
+  const float2 P = make_float2(t.x, t.y), Q = make_float2(t.z, t.w);
+  // sin(theta) = -w.y, cos(theta) = w.x
+  float2 al = make_float2(fmaf(w.y, Q.x, P.x), fmaf(w.y, Q.y, P.y));
+  float2 al2 = make_float2(fmaf(-w.y, Q.x, P.x), -fmaf(-w.y, Q.y, P.y));
+  float2 be = make_float2(-w.x * Q.y, w.x * Q.x);
   float2 be2 = make_float2(-be.x, be.y);
   if (!ADJ) {
     al = cconj(al);
@@ -334,8 +341,12 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
       int ea, eb, k2, k1, tidx;
       slot_at(t, ea, eb, k2, k1, tidx);
       float2 za = sm[pad(ea)], zb = sm[pad(eb)];
-      if (KIND == MID_ADMM) op_admm(kp.pp, a_rho, a_sigma, tidx, za, zb);
-      else op_real<KIND == MID_ADJ>(kp.pp, tidx, za, zb);
+      if (KIND == MID_ADMM) {
+        op_admm(kp.pp, a_rho, a_sigma, tidx, za, zb);
+      } else {
+        const float2 w = TWOD ? __ldg(g.tw1 + k1) : cmul(__ldg(g.twr + k2), __ldg(g.tw1 + k1));
+        op_real<KIND == MID_ADJ>(kp.pp, tidx, w, za, zb);
+      }
       sm[pad(eb)] = zb;   // self-pairs (ea == eb) keep the k-side value
       sm[pad(ea)] = za;
     }

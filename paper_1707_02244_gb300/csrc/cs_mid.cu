@@ -336,7 +336,9 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
   } else {
     load_tile(sm, W);
     fwd_rows(sm);
-    // spectrum operator over all (k, N-k) pairs held by this CTA
+    // spectrum operator over all (k, N-k) pairs held by this CTA (unrolled so
+    // that the table loads of several slots are in flight together)
+#pragma unroll 4
     for (int t = threadIdx.x; t < nslots; t += NT) {
       int ea, eb, k2, k1, tidx;
       slot_at(t, ea, eb, k2, k1, tidx);

@@ -231,13 +231,15 @@ cs_status cs_batch_admm(cs_batch_t batch, const float* y, const float* lambda,
                         const float* rho, int iters, float* z);
 
 /* Waits for the batch's work; returns CS_ERR_NONFINITE if a measurement was
- * not finite, else the first error latched by a per-instance plan. */
+ * not finite, else the first error latched by a per-instance plan.  The
+ * latched status is cleared (each condition is reported once). */
 cs_status cs_batch_status_sync(cs_batch_t batch);
 
 /* Direct circulant product (context comparator; Sec. 5.2's scheme of one
  * O(n) dot product per output, not the FFT path).  No plan:
  *   c     DEVICE float[n]: first row of C (fp32)
- *   rows  DEVICE int32[m]: kept rows, 0 <= rows[i] < n (not checked)
+ *   rows  DEVICE int32[m]: kept rows, 0 <= rows[i] < n (a row outside
+ *         that range is not read from; its y[i] is NaN)
  *   x     DEVICE float[n];  y DEVICE float[m] receives (A x)_i = (C x)_{rows[i]}
  * O(m n) work, one warp per row.  Asynchronous on `stream`. */
 cs_status cs_forward_direct(int64_t n, int64_t m, const float* c, const int32_t* rows,

@@ -732,6 +732,8 @@ cs_status cs_batch_status_sync(cs_batch_t b) {
     int hs = 0;
     st = cstat(cudaMemcpy(&hs, b->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != CS_OK) return st;
+    st = cstat(cudaMemset(b->status, 0, sizeof(int)));   // reported once, as cs_status_sync
+    if (st != CS_OK) return st;
     if (hs & STS_NONFINITE) return CS_ERR_NONFINITE;
   }
   return CS_OK;

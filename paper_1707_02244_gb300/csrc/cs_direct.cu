@@ -19,6 +19,10 @@ __global__ void __launch_bounds__(32 * DW) direct_forward_k(const float* __restr
   const int lane = threadIdx.x & 31;
   if (i >= m) return;
   const int64_t r = rows[i];
+  if (r < 0 || r >= n) {   // invalid row: no access, NaN result
+    if (lane == 0) y[i] = __int_as_float(0x7fc00000);
+    return;
+  }
   float acc = 0.f;
   // j = lane + 32 q; c index (j - r) mod n: contiguous across the warp
   for (int64_t j = lane; j < n; j += 32) {

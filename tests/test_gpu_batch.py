@@ -148,5 +148,9 @@ def test_batch_rejects_nonfinite_measurements(cs):
         x = torch.zeros(int(n.sum()), dtype=torch.float32, device=dev)
         cs.cs_batch_ista(b, to_dev(y), 1e-3, 0.1, 5, x)
         assert cs.cs_batch_status_sync(b) == cs.CS_ERR_NONFINITE
+        # reported once; a finite call afterwards is clean
+        y[57] = 0.0
+        cs.cs_batch_ista(b, to_dev(y), 1e-3, 0.1, 5, x)
+        assert cs.cs_batch_status_sync(b) == cs.CS_OK
     finally:
         b.close()

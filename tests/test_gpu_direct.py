@@ -26,3 +26,18 @@ def test_direct_forward_matches_oracle(n, m):
     got = host(y)
     assert rel_l2(got, want) <= 2e-6, rel_l2(got, want)
     assert np.max(np.abs(got - want)) <= 2e-5 * np.sqrt(np.mean(want ** 2)) * np.sqrt(n / 1024 + 1)
+
+
+def test_direct_forward_invalid_row_is_nan_not_a_read():
+    import paper_1707_02244_gb300 as cs
+    torch, dev = torch_dev()
+    n, m = 256, 4
+    c = to_dev(synth.random_vector(n, 9050).astype(np.float32))
+    x = to_dev(synth.random_vector(n, 9051).astype(np.float32))
+    rows = torch.tensor([3, -1, n, 7], dtype=torch.int32, device=dev)
+    y = torch.zeros(m, dtype=torch.float32, device=dev)
+    cs.cs_forward_direct(n, m, c, rows, x, y, torch.cuda.current_stream(dev))
+    torch.cuda.synchronize()
+    got = host(y)
+    assert np.isfinite(got[0]) and np.isfinite(got[3])
+    assert np.isnan(got[1]) and np.isnan(got[2])

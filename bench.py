@@ -73,6 +73,27 @@ def dist_env():
     return rank, world, local
 
 
+def replica_seed(rank):
+    """Each rank solves its own instance (replicas, no data-path collective)."""
+    return synth.LARGE_SEED + rank
+
+
+def max_over_ranks(seconds, world, device):
+    """The job's time: the slowest rank's (a single process: unchanged)."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput: units of all ranks over the job's time."""
+    return world * units_per_rank / seconds
+
+
 def peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -246,7 +267,7 @@ def run_gpu(args):
     import paper_1707_02244_gb300 as cs
 
     stream = torch.cuda.current_stream(dev)
-    inst = synth.large_instance(seed=synth.LARGE_SEED + rank, n=args.n)
+    inst = synth.large_instance(seed=replica_seed(rank), n=args.n)
     n, m, T = inst.n, inst.m, args.iters
 
     torch.cuda.synchronize()
@@ -295,12 +316,8 @@ def run_gpu(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * 2 * T * args.steps / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    value = job_rate(world, 2 * T * args.steps, total_s)
 
     # e2e through the public API: pinned host y in, x and z out, every step
     y_h = torch.empty(m, dtype=torch.float32, pin_memory=True)
@@ -321,8 +338,8 @@ def run_gpu(args):
         z_h.copy_(z, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
-    e2e_value = world * 2 * T * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
+    e2e_value = job_rate(world, 2 * T * e2e_steps, e2e_s)
 
     extras = {}
     roof = None

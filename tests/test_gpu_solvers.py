@@ -311,3 +311,26 @@ def test_ista_and_admm_reach_the_same_minimiser(cs):
     A = O.sensing_matrix(inst.c, inst.rows)
     assert O.kkt_violation(A, y32.astype(np.float64), host(x), lam) <= 1e-5
     assert rel_l2(g["z"], host(x)) <= 1e-4
+
+
+def test_graphs_match_direct_launches(cs, monkeypatch):
+    """The captured-graph chunks (default) and direct launches (CS_GRAPHS=0)
+    run the same kernels in the same order: results are bit-identical, for
+    iteration counts that are not multiples of the chunk length."""
+    torch, dev = torch_dev()
+    inst = synth.instance(1 << 14, 1 << 12, k=40, noise_std=1e-3, seed=71)
+    y32 = _y32(inst, dense=False)
+    outs = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("CS_GRAPHS", mode)
+        plan = _plan(cs, inst)
+        try:
+            x = torch.zeros(inst.n, dtype=torch.float32, device=dev)
+            cs.cs_ista(plan, to_dev(y32), f32(2e-3), f32(0.05), 37, x)
+            z = torch.zeros(inst.n, dtype=torch.float32, device=dev)
+            cs.cs_admm(plan, to_dev(y32), f32(2e-3), 1.0, 23, z)
+            outs[mode] = (host(x), host(z))
+        finally:
+            plan.close()
+    assert np.array_equal(outs["1"][0], outs["0"][0])
+    assert np.array_equal(outs["1"][1], outs["0"][1])

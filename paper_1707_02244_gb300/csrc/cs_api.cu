@@ -118,7 +118,7 @@ void make_geo2d(Geo& g, int lgN2, int lgN1) {
   g.N2 = 1 << lgN2;
   g.lgN1 = lgN1;
   g.N1 = 1 << lgN1;
-  const int lgCol = lgN2 <= 11 ? 12 : 13;
+  const int lgCol = lgN2 <= 11 ? 12 : 14;
   g.col_tile = 1 << lgCol;
   g.lgG = (lgCol - lgN2) < lgN1 ? (lgCol - lgN2) : lgN1;
   g.G = 1 << g.lgG;
@@ -139,7 +139,7 @@ bool geo_ok(const Geo& g) {
   if (g.twod)
     return g.N2 >= 2 && g.N1 >= 2 && g.G >= 2 && g.col_ctas >= 1 && g.mid_ctas >= 1 && g.U >= 1 &&
            2 * g.U <= 64 && (2 * g.U) * g.N1 <= g.tile && (g.G << g.lgN2) <= g.col_tile && g.N1 <= 4096 &&
-           (g.col_tile == 4096 || (g.lgN2 == 12 && g.lgG == 1));
+           (g.col_tile == 4096 || (g.lgN2 == 12 && g.lgG == 2 && g.col_tile == 16384));
   return g.N1 >= g.N2 && g.N2 >= 2 && g.G >= 2 && g.col_ctas >= 1 && g.mid_ctas >= 1 &&
          2 * g.U <= 64 && (2 * g.U) * g.N1 <= g.tile && (g.G << g.lgN2) <= 4096;
 }

@@ -11,12 +11,13 @@ namespace {
 // ---------------------------------------------------------------- column pass
 
 // The column pass uses 4096-value tiles (4 CTAs per SM; 1D: N2 <= 1024
-// gives G >= 4 columns), and 8192-value tiles of two 4096-long columns for
-// 2D arrays of 4096 rows (2 CTAs per SM).
+// gives G >= 4 columns), and 16384-value tiles of four 4096-long columns for
+// 2D arrays of 4096 rows (1 CTA per SM): four columns make each row of the
+// exchange buffer a full 32-byte sector (two would use half of it).
 constexpr int COL_TILE = 4096;
 constexpr int COL_MINB = 4;
-constexpr int COL_TILE2 = 8192;
-constexpr int COL_MINB2 = 2;
+constexpr int COL_TILE4 = 16384;
+constexpr int COL_MINB4 = 1;
 
 // Epilogue as the post hook of the inverse column FFT: runs on each value as
 // the last stage produces it, so the elementwise step costs no extra pass
@@ -53,18 +54,19 @@ template <> struct ColShape<1> {
   __device__ static constexpr int lgG(const Geo&) { return 2; }
   __device__ static constexpr int lgN2(const Geo&) { return 10; }
 };
-// SHAPE 2: N2 = 4096 and G = 2 (2D arrays of 4096 rows), 8192-value tiles.
-template <> struct ColShape<2> {
-  using Lay = StaticLayout<12, 1, true>;
+
+// SHAPE 3: N2 = 4096 and G = 4, 16384-value tiles (1024 threads).
+template <> struct ColShape<3> {
+  using Lay = StaticLayout<12, 2, true>;
   __device__ static Lay lay(const Geo&) { return Lay{}; }
-  __device__ static constexpr int lgG(const Geo&) { return 1; }
+  __device__ static constexpr int lgG(const Geo&) { return 2; }
   __device__ static constexpr int lgN2(const Geo&) { return 12; }
 };
 
 template <int SHAPE> struct ColTile {
-  static constexpr int kTile = SHAPE == 2 ? COL_TILE2 : COL_TILE;
-  static constexpr int kMinB = SHAPE == 2 ? COL_MINB2 : COL_MINB;
-  static constexpr int kLgN2 = SHAPE == 2 ? 12 : 10;   // static shapes
+  static constexpr int kTile = SHAPE == 3 ? COL_TILE4 : COL_TILE;
+  static constexpr int kMinB = SHAPE == 3 ? COL_MINB4 : COL_MINB;
+  static constexpr int kLgN2 = SHAPE == 3 ? 12 : 10;   // static shapes
 };
 
 template <int KIND, int SHAPE>
@@ -202,7 +204,7 @@ cudaError_t init_col_kernels() {
   if (e == cudaSuccess) e = set_smem(col_kernel<k, S>, ColTile<S>::kTile, ColTile<S>::kMinB);
   CS_COL_KINDS(CS_SET_COL, 0)
   CS_COL_KINDS(CS_SET_COL, 1)
-  CS_COL_KINDS_2D(CS_SET_COL, 2)
+  CS_COL_KINDS_2D(CS_SET_COL, 3)
 #undef CS_SET_COL
   return e;
 }
@@ -212,9 +214,9 @@ cudaError_t launch_col(ColKind kind, const KParams& kp, cudaStream_t s) {
   const int grid = g.col_ctas;
   const bool hot = g.lgN2 == 10 && g.lgG == 2;
 #define CS_L_COL(k, S) case k: return launch_k(col_kernel<k, S>, grid, ColTile<S>::kTile, kp, s);
-  if (g.col_tile == COL_TILE2) {
-    if (g.lgN2 == 12 && g.lgG == 1) {
-      switch (kind) { CS_COL_KINDS_2D(CS_L_COL, 2) default: break; }
+  if (g.col_tile == COL_TILE4) {
+    if (g.lgN2 == 12 && g.lgG == 2) {
+      switch (kind) { CS_COL_KINDS_2D(CS_L_COL, 3) default: break; }
     }
   } else if (hot) {
     switch (kind) { CS_COL_KINDS(CS_L_COL, 1) }

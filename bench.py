@@ -37,6 +37,7 @@ import pathlib
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -163,7 +164,7 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = ROOT / "gpurun_out" / f"clocks_{os.getpid()}.csv"
+        self.path = pathlib.Path(tempfile.gettempdir()) / f"csgb_clocks_{os.getpid()}_{index}.csv"
 
     def start(self):
         try:

@@ -17,7 +17,8 @@
  *   - The caller owns every vector it passes; the plan owns all of its own
  *     memory (spectrum, tables, exchange buffer) and frees it in
  *     cs_plan_destroy.  The plan copies `rows` and `c`.
- *   - n must be a power of two with 64 <= n <= 4194304 (2^22); 1 <= m <= n.
+ *   - cs_plan: n a power of two with 64 <= n <= 4194304 (2^22); 1 <= m <= n.
+ *     cs_plan_2d: n = n0 n1 up to 4096 x 4096 (limits at that call).
  *   - Argument errors are returned at once and nothing is launched.
  *     Errors found on the device (non-finite input, a wait that ran out) are
  *     latched in the plan and returned by cs_status_sync or by the next call

@@ -116,6 +116,25 @@ def batch_instances(n, m, *, k_frac: float = 0.01, noise_std: float = 1e-3, seed
 STAR_SEED = 1707002
 
 
+def box_blur_c(n: int, L: int = 5) -> np.ndarray:
+    """First row of the order-L box blur (its first L entries 1/L)."""
+    b = np.zeros(n)
+    b[:L] = 1.0 / L
+    return b
+
+
+def composite_c(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """First row of C(a) C(b) for first-row circulants (C[i][j] = a[(j - i)
+    mod n]): entry s is sum_d a[d] b[(s - d) mod n], summed over the nonzeros
+    of b (a short filter)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    out = np.zeros_like(a)
+    for e in np.flatnonzero(b):
+        out += b[e] * np.roll(a, e)
+    return out
+
+
 def gaussian_psf(sigma: float = 2.5, support: int = 15) -> np.ndarray:
     """support x support Gaussian point-spread function, normalised to sum 1."""
     h = support // 2

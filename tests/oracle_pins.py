@@ -375,6 +375,22 @@ def check_unrolled_grad_dense_fft_agree(O):
     assert abs(fd - float(np.dot(gf["dc"], d))) <= 1e-6 * max(1.0, abs(fd))
 
 
+def check_product_of_circulants(O):
+    """Sec. 7: the product of circulant matrices is circulant (A = C B for a
+    circulant sensing C and blur B).  C(a) C(b), formed densely, equals the
+    circulant of the generating vector the input generator builds for it,
+    for a box blur of order 5 and for a random short filter."""
+    g = synth.rng(161)
+    for n, b in ((16, synth.box_blur_c(16, 5)), (12, np.r_[g.standard_normal(3), np.zeros(9)])):
+        a = g.standard_normal(n)
+        prod = O.circulant_matrix(a) @ O.circulant_matrix(b)
+        assert np.allclose(prod, O.circulant_matrix(synth.composite_c(a, b)), atol=1e-12), n
+    # the box blur averages L consecutive entries (its definition)
+    x = g.standard_normal(16)
+    bx = O.circulant_matrix(synth.box_blur_c(16, 5)) @ x
+    assert np.allclose(bx, [np.mean(x[np.arange(i, i + 5) % 16]) for i in range(16)], atol=1e-14)
+
+
 # ---------------------------------------------------------------- 2D operator
 
 def check_2d_separable_is_kronecker(O):
@@ -459,5 +475,5 @@ ALL_CHECKS = [
     check_exact_recovery_tiny, check_admm_inverse, check_dense_fft_agree,
     check_opnorm, check_unrolled_grad_finite_differences, check_unrolled_grad_dense_fft_agree,
     check_2d_separable_is_kronecker, check_2d_eigenvectors, check_2d_point_source_is_psf,
-    check_2d_fft_matches_dense,
+    check_2d_fft_matches_dense, check_product_of_circulants,
 ]

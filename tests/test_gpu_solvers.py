@@ -334,3 +334,34 @@ def test_graphs_match_direct_launches(cs, monkeypatch):
             plan.close()
     assert np.array_equal(outs["1"][0], outs["0"][0])
     assert np.array_equal(outs["1"][1], outs["0"][1])
+
+
+def test_compressed_deblurring_1d(cs):
+    """Sec. 7's setting in one dimension: A = P C B, C a random circulant,
+    B the order-5 box blur, m = n/2; the plan takes the generating vector of
+    the product C B.  A x matches C applied to B x (two oracle products), and
+    ISTA matches the oracle on the composite operator."""
+    torch, dev = torch_dev()
+    n, m = 1 << 16, 1 << 15
+    inst = synth.instance(n, m, k=n // 10, noise_std=1e-3, seed=73)
+    cB = synth.composite_c(inst.c, synth.box_blur_c(n, 5))
+    chB = O.spectrum(cB)
+    ch, hb = O.spectrum(inst.c), O.spectrum(synth.box_blur_c(n, 5))
+    x = inst.x_true
+    want = O.circulant_apply_fft(ch, O.circulant_apply_fft(hb, x))[inst.rows]
+    y32 = (want + inst.noise).astype(np.float32)
+    lam = f32(1e-2)
+    tau = f32(1.0 / np.max(np.abs(chB) ** 2))
+    plan = cs.cs_plan(n, m, inst.rows, cB, torch.cuda.current_stream(dev))
+    try:
+        yg = torch.empty(m, dtype=torch.float32, device=dev)
+        cs.cs_forward(plan, to_dev(x), yg)
+        xg = torch.zeros(n, dtype=torch.float32, device=dev)
+        cs.cs_ista(plan, to_dev(y32), lam, tau, 100, xg)
+        torch.cuda.synchronize()
+        got_y, got_x = host(yg), host(xg)
+    finally:
+        plan.close()
+    assert rel_l2(got_y, want) <= 2e-6, rel_l2(got_y, want)
+    xo = O.ista_fft(cB, inst.rows, y32.astype(np.float64), lam, tau, 100)
+    assert rel_l2(got_x, xo) <= ITER_TOL, rel_l2(got_x, xo)

@@ -127,3 +127,26 @@ def test_plan_2d_rejects_bad_arguments_without_device(cs):
     for n0, n1 in ((8, 8), (4, 16), (8192, 16), (12, 16), (8, 24)):
         assert cs.raw_call("cs_plan_2d", ctypes.byref(h), n0, n1, 8, pix.ctypes.data, c2.ctypes.data,
                            None) == cs.CS_ERR_UNSUPPORTED, (n0, n1)
+
+
+def _declared_arity():
+    """Parameter count of every call declared in the header."""
+    text = re.sub(r"/\*.*?\*/", "", HEADER.read_text(), flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(cs_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        p = params.strip()
+        out[name] = 0 if p in ("", "void") else len([x for x in p.split(",") if x.strip()])
+    return out
+
+
+def test_binding_signatures_match_header(cs):
+    """Every entry point the binding sets argtypes for takes as many
+    arguments as the header declares (a mismatch would corrupt the call)."""
+    arity = _declared_arity()
+    lib = cs._lib
+    for name in cs.EXPORTS:
+        fn = getattr(lib, name)
+        if fn.argtypes is None:
+            continue
+        assert name in arity, name
+        assert len(fn.argtypes) == arity[name], (name, len(fn.argtypes), arity[name])

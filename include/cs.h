@@ -264,10 +264,14 @@ cs_status cs_forward_direct(int64_t n, int64_t m, const float* c, const int32_t*
  * Computed in FP64 (FFT of c and x, spectrum product, inverse FFT), rounded
  * to fp32 once.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call uses the same array and
- * overwrites all of it that it reads, so calls that overlap on the GPU race:
- * order them on one stream.  Asynchronous; errors: CS_ERR_ARG (null pointer),
- * CS_ERR_UNSUPPORTED (n), CS_ERR_CUDA. */
+ * call before any stream capture.  The lookup is kept per device and
+ * repeated when the device's current CUDA context has changed since (as
+ * after cudaDeviceReset).  Every call uses the same array and overwrites all
+ * of it that it reads, so calls that overlap on the GPU race: order them on
+ * one stream.  Asynchronous; errors: CS_ERR_ARG (null pointer),
+ * CS_ERR_UNSUPPORTED (n), CS_ERR_CUDA (a launch failed, or a CUDA error was
+ * already pending on the calling thread when the call started: that error is
+ * left pending for its owner and nothing is launched). */
 cs_status cs_circulant_apply_static(int64_t n, const double* c, const float* x, float* y,
                                     int transpose, void* stream);
 

@@ -100,19 +100,23 @@ def cs_version() -> int:
     return int(_lib.cs_version())
 
 
-def _ptr(t) -> int | None:
-    """Device address of a tensor-like (torch tensor, int, None)."""
+def _ptr(t, dtype: str = "torch.float32", numel: int | None = None) -> int | None:
+    """Device address of a tensor-like (torch tensor, int, None).  A tensor
+    must be a contiguous CUDA tensor of `dtype` holding at least `numel`
+    elements (when given); a raw int address is passed through unchecked."""
     if t is None:
         return None
     if isinstance(t, int):
         return t
     if hasattr(t, "data_ptr"):
-        if getattr(t, "dtype", None) is not None and str(t.dtype) != "torch.float32":
-            raise TypeError(f"expected float32, got {t.dtype}")
+        if getattr(t, "dtype", None) is not None and str(t.dtype) != dtype:
+            raise TypeError(f"expected {dtype.split('.')[-1]}, got {t.dtype}")
         if hasattr(t, "is_contiguous") and not t.is_contiguous():
             raise ValueError("expected a contiguous tensor")
         if hasattr(t, "is_cuda") and not t.is_cuda:
             raise ValueError("expected a CUDA tensor")
+        if numel is not None and t.numel() < numel:
+            raise ValueError(f"expected at least {numel} elements, got {t.numel()}")
         return int(t.data_ptr())
     raise TypeError(f"cannot take a device pointer of {type(t)!r}")
 
@@ -292,10 +296,13 @@ def cs_profile_pass(plan: Plan, pass_id: int, reps: int = 1):
 
 
 def cs_circulant_apply_static(n: int, c, x, y, transpose: bool = False, stream=None):
-    """y = C x (or C^T x) with no plan and no allocation (n <= 16384);
-    c is a float64 device tensor / address, x and y float32."""
-    cptr = int(c.data_ptr()) if hasattr(c, "data_ptr") else int(c)
-    _check(_lib.cs_circulant_apply_static(int(n), cptr, _ptr(x), _ptr(y), int(bool(transpose)),
+    """y = C x (or C^T x) with no plan and no allocation (n <= 16384).
+    c: float64 CUDA tensor (or device address) of at least n elements; x, y:
+    float32 CUDA tensors of at least n elements.  Tensors of another dtype,
+    on the host or too short are rejected here, before anything is launched."""
+    n = int(n)
+    cptr = _ptr(c, dtype="torch.float64", numel=n)
+    _check(_lib.cs_circulant_apply_static(n, cptr, _ptr(x, numel=n), _ptr(y, numel=n), int(bool(transpose)),
                                           _stream_handle(stream)), "cs_circulant_apply_static")
 
 

@@ -28,24 +28,54 @@ static __device__ __align__(256) double2 g_static_scratch[3 * kStaticMaxN];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-double2* g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+  void* ctx = nullptr;        // CUDA context the address belongs to
+  double2* addr = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
 
-// Device address of the array for the current device.  In host code the
+// cuCtxGetCurrent from the driver, fetched through the runtime so that the
+// library needs no link against libcuda.
+using CtxGetCurrentFn = int (*)(void**);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  return fn;
+}
+
+// Device address of the array in the current context.  In host code the
 // array's name is only a host-side stand-in, so the address comes from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, looked up once per device with that device current.
+// The lookup is repeated when the device's current context is another one
+// than at the last lookup (after cudaDeviceReset the module, and with it the
+// array, can be loaded at another address).
 cudaError_t scratch_address(double2** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get) return cudaErrorInitializationError;
+  // null before the runtime has made a context current on this thread
+  void* ctx = nullptr;
+  if (get(&ctx) != 0) return cudaErrorInitializationError;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  ScratchAddr& sa = g_scratch_addr[dev];
+  if (!sa.addr || !ctx || sa.ctx != ctx) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    e = cudaGetSymbolAddress(&p, g_static_scratch);   // makes the device's primary context current if none is
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double2*>(p);
+    if (get(&ctx) != 0 || !ctx) return cudaErrorInitializationError;
+    sa.addr = static_cast<double2*>(p);
+    sa.ctx = ctx;
   }
-  *out = g_scratch_addr[dev];
+  *out = sa.addr;
   return cudaSuccess;
 }
 
@@ -89,6 +119,9 @@ extern "C" cs_status cs_circulant_apply_static(int64_t n, const double* c, const
                                                int transpose, void* stream) {
   if (!c || !x || !y) return CS_ERR_ARG;
   if (n < 64 || n > kStaticMaxN || (n & (n - 1)) != 0) return CS_ERR_UNSUPPORTED;
+  // An error the caller left pending on this thread is not this call's: leave
+  // it in place (peek does not clear it) and launch nothing.
+  if (cudaPeekAtLastError() != cudaSuccess) return CS_ERR_CUDA;
   double2* base = nullptr;
   cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return CS_ERR_CUDA;
@@ -96,6 +129,7 @@ extern "C" cs_status cs_circulant_apply_static(int64_t n, const double* c, const
   double2* buf[3] = {base, base + n, base + 2 * n};
   // chat = FFT(c) in buffers 0 / 1
   real_to_complex64_k<<<nblk(n), NTH, 0, s>>>(c, buf[0], n);
+  if (cudaGetLastError() != cudaSuccess) return CS_ERR_CUDA;
   double2* chat = nullptr;
   e = launch_fft64_complex(buf[0], buf[1], n, &chat, s);
   if (e != cudaSuccess) return CS_ERR_CUDA;
@@ -103,11 +137,13 @@ extern "C" cs_status cs_circulant_apply_static(int64_t n, const double* c, const
   double2* f1 = buf[2];
   // X = FFT(x)
   float_to_complex64_k<<<nblk(n), NTH, 0, s>>>(x, f0, n);
+  if (cudaGetLastError() != cudaSuccess) return CS_ERR_CUDA;
   double2* X = nullptr;
   e = launch_fft64_complex(f0, f1, n, &X, s);
   if (e != cudaSuccess) return CS_ERR_CUDA;
   double2* w = X == f0 ? f1 : f0;
   spectrum_product_k<<<nblk(n), NTH, 0, s>>>(chat, X, w, n, transpose ? 1 : 0);
+  if (cudaGetLastError() != cudaSuccess) return CS_ERR_CUDA;
   double2* R = nullptr;
   e = launch_fft64_complex(w, X, n, &R, s);
   if (e != cudaSuccess) return CS_ERR_CUDA;

@@ -150,3 +150,25 @@ def test_binding_signatures_match_header(cs):
             continue
         assert name in arity, name
         assert len(fn.argtypes) == arity[name], (name, len(fn.argtypes), arity[name])
+
+
+def test_static_product_binding_rejects_bad_tensors_before_any_launch(cs):
+    """cs_circulant_apply_static's binding checks dtype, residency and length
+    of c, x and y before the library is called (no device is touched)."""
+    import torch
+    n = 64
+    c64 = torch.zeros(n, dtype=torch.float64)        # host tensor
+    c32 = torch.zeros(n, dtype=torch.float32)
+    x = torch.zeros(n, dtype=torch.float32)
+    with pytest.raises(TypeError):                   # float32 c: 4n bytes where 8n are read
+        cs.cs_circulant_apply_static(n, c32, x, x)
+    with pytest.raises(ValueError):                  # host c
+        cs.cs_circulant_apply_static(n, c64, x, x)
+
+
+def test_ptr_checks_length(cs):
+    import torch
+    with pytest.raises(ValueError):
+        cs._ptr(torch.zeros(4, dtype=torch.float32), numel=8)
+    with pytest.raises(TypeError):
+        cs._ptr(torch.zeros(4, dtype=torch.float64))

@@ -17,6 +17,18 @@ spectrum, tables) and the power iteration are set-up, reported separately.
   python bench.py --workload grad [--steps K] [--warmup W]
   python bench.py --workload context
   python bench.py --workload deblur2d [--steps K] [--warmup W] [--iters T]
+  CS_GRAPHS=0 python bench.py --workload profile-iter|profile-passes|profile-batch|profile-2d|profile-grad
+
+The profile-* workloads are short fixed launch sequences for ncu captures
+(nothing is timed; with CS_GRAPHS=0 every kernel is its own launch, so ncu's
+-k / -s / -c pick single passes):
+  profile-iter    n = 2^22: 3 ISTA and 3 ADMM iterations;
+  profile-passes  n = 2^22: 3 ISTA iterations, then each ISTA pass kernel 3
+                  times back to back (L2 as inside a solve);
+  profile-batch   128 instances (64 of n = 8192, 64 of 4096), 5 ISTA and 5
+                  ADMM iterations in the single-CTA kernels;
+  profile-2d      the 4096 x 4096 star field, 3 ISTA and 3 ADMM iterations;
+  profile-grad    n = 2^20, m = n/4, 4 unrolled ISTA steps, checkpoints every 2.
 
 The batched workload: 512 independent instances, n log-uniform in
 [2^12, 2^20] (snapped to powers of two), m/n uniform in [0.2, 0.5], k/n =
@@ -62,7 +74,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=1 << 22)
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-NMSE, roofline and CPU legs")
-    ap.add_argument("--workload", default="n2e22", choices=["n2e22", "batched", "grad", "context", "deblur2d"])
+    ap.add_argument("--workload", default="n2e22",
+                    choices=["n2e22", "batched", "grad", "context", "deblur2d",
+                             "profile-iter", "profile-passes", "profile-batch", "profile-2d", "profile-grad"])
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched workload")
     return ap.parse_args()
 
@@ -118,19 +132,41 @@ def oracle_sample(inst, iters_each):
     return time.perf_counter() - t0, 2 * iters_each
 
 
-def cpu_baseline(inst):
-    secs, its = oracle_sample(inst, 6)
-    return {"value": its / secs, "unit": "iter/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle, {its // 2} ISTA + {its // 2} ADMM iterations at n=2^22 "
-                      f"({secs:.1f} s; numpy FFT runs on one thread)"}
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(inst, iters_each=6):
+    """The FP64 oracle on the host: once with its default one-thread FFT step,
+    once with the FFT step on every host core (scipy's FFT with a worker
+    pool); `value` and `cores` are those of the all-core run."""
+    import oracle.cs_oracle as O
+    nproc = host_cores()
+    secs1, its = oracle_sample(inst, iters_each)
+    old = O.set_fft_threads(nproc)
+    try:
+        secsN, _ = oracle_sample(inst, iters_each)
+    finally:
+        O.set_fft_threads(old)
+    return {"value": its / secsN, "unit": "iter/s", "cores": nproc, "kind": "oracle",
+            "value_1_thread": its / secs1, "nproc": nproc,
+            "sample": f"FP64 oracle, {its // 2} ISTA + {its // 2} ADMM iterations at n=2^22, FFT step on "
+                      f"{nproc} threads ({secsN:.1f} s) and on 1 thread ({secs1:.1f} s); the rest of the "
+                      f"oracle's numpy arithmetic runs on one thread"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    import oracle.cs_oracle as O
     inst = synth.large_instance(n=args.n)
     per = 1
+    nproc = host_cores()
+    O.set_fft_threads(nproc)
     for _ in range(args.warmup):
         oracle_sample(inst, per)
     times = []
@@ -146,8 +182,9 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": inst.n, "m": inst.m,
                    "step": f"{per} ISTA + {per} ADMM iterations (bounded sample of the GPU step)"},
-        "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{per} ISTA + {per} ADMM FP64 oracle iterations per step"},
+        "cpu_baseline": {"value": value, "unit": "iter/s", "cores": nproc, "kind": "oracle", "nproc": nproc,
+                         "sample": f"{per} ISTA + {per} ADMM FP64 oracle iterations per step, FFT step on "
+                                   f"{nproc} threads"},
         "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -824,8 +861,75 @@ def run_deblur2d(args):
     return 0
 
 
+def run_profile(args):
+    """Fixed launch sequences for ncu (see the module docstring)."""
+    import torch
+    import paper_1707_02244_gb300 as cs
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    mode = args.workload
+    if mode in ("profile-iter", "profile-passes"):
+        inst = synth.large_instance(n=args.n)
+        plan = cs.cs_plan(inst.n, inst.m, inst.rows, inst.c, stream)
+        xt = torch.from_numpy(inst.x_true.astype(np.float32)).to(dev)
+        y = torch.empty(inst.m, dtype=torch.float32, device=dev)
+        cs.cs_forward(plan, xt, y)
+        x = torch.zeros(inst.n, dtype=torch.float32, device=dev)
+        cs.cs_ista(plan, y, LAM, 0.05, 3, x)
+        if mode == "profile-iter":
+            z = torch.zeros(inst.n, dtype=torch.float32, device=dev)
+            cs.cs_admm(plan, y, LAM, RHO, 3, z)
+        else:
+            for pid in range(4):
+                cs.cs_profile_pass(plan, pid, 3)
+        plan.close()
+    elif mode == "profile-batch":
+        n = np.array([8192] * 64 + [4096] * 64, dtype=np.int64)
+        m = n // 4
+        insts = synth.batch_instances(n, m)
+        b = cs.cs_batch_plan(n, m, np.concatenate([i.rows for i in insts]), np.concatenate([i.c for i in insts]),
+                             stream)
+        y = torch.from_numpy(np.random.default_rng(0).standard_normal(int(m.sum())).astype(np.float32)).to(dev)
+        x = torch.zeros(int(n.sum()), dtype=torch.float32, device=dev)
+        z = torch.zeros_like(x)
+        cs.cs_batch_ista(b, y, 1e-3, 0.05, 5, x)
+        cs.cs_batch_admm(b, y, 1e-3, 1.0, 5, z)
+        assert cs.cs_batch_status_sync(b) == cs.CS_OK
+        b.close()
+    elif mode == "profile-2d":
+        img = synth.star_field()
+        plan = cs.cs_plan_2d(img.n0, img.n1, img.m, img.pix, img.c2, stream)
+        xt = torch.from_numpy(img.x_true.astype(np.float32)).to(dev)
+        y = torch.empty(img.m, dtype=torch.float32, device=dev)
+        cs.cs_forward(plan, xt, y)
+        x = torch.zeros(img.n, dtype=torch.float32, device=dev)
+        z = torch.zeros_like(x)
+        cs.cs_ista(plan, y, 2e-4, 1.0, 3, x)
+        cs.cs_admm(plan, y, 2e-4, 1.0, 3, z)
+        plan.close()
+    else:   # profile-grad
+        n = 1 << 20
+        inst = synth.instance(n, n // 4, k=n // 100, noise_std=1e-3, seed=8300)
+        plan = cs.cs_plan(n, inst.m, inst.rows, inst.c, stream)
+        xt = torch.from_numpy(inst.x_true.astype(np.float32)).to(dev)
+        y = torch.empty(inst.m, dtype=torch.float32, device=dev)
+        cs.cs_forward(plan, xt, y)
+        gx = torch.ones(n, dtype=torch.float32, device=dev)
+        dc = torch.empty(n, dtype=torch.float32, device=dev)
+        dl = torch.empty(1, dtype=torch.float32, device=dev)
+        dy = torch.empty(inst.m, dtype=torch.float32, device=dev)
+        cs.cs_grad(plan, y, 5e-3, 0.05, 4, 2, gx, dc, dl, dy)
+        assert cs.cs_status_sync(plan) == cs.CS_OK
+        plan.close()
+    torch.cuda.synchronize()
+    print(f"{mode} ok", flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload.startswith("profile-"):
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":

@@ -43,7 +43,47 @@ __all__ = [
     "ista_unrolled_grad_dense", "ista_unrolled_grad_fft", "ista_unrolled_loss",
     "circulant2d_matrix", "sensing2d_matrix", "spectrum2d", "circulant2d_apply_fft", "forward2d_fft",
     "adjoint2d_fft", "ista_dense2d", "ista_fft2d", "admm_dense2d", "admm_fft2d", "naive_dft2",
+    "set_fft_threads",
 ]
+
+
+# --------------------------------------------------------------------------
+# FFT library step
+# --------------------------------------------------------------------------
+
+class _FFT:
+    """The FFT used as a library step by the FFT forms below: numpy's (one
+    thread) by default; scipy's with a worker pool after set_fft_threads(k),
+    k > 1 (used to time the oracle on all host cores).  Both compute the same
+    DFT; they may differ in the last bits of rounding."""
+    threads = 1
+
+    @classmethod
+    def _lib(cls):
+        if cls.threads > 1:
+            import scipy.fft as sf
+            return sf, {"workers": cls.threads}
+        return np.fft, {}
+
+    @classmethod
+    def call(cls, name, *a, **kw):
+        lib, extra = cls._lib()
+        return getattr(lib, name)(*a, **kw, **extra)
+
+
+def set_fft_threads(k: int) -> int:
+    """Threads for the FFT library step (1 = numpy); returns the old value."""
+    old = _FFT.threads
+    _FFT.threads = max(1, int(k))
+    return old
+
+
+def _fft(a): return _FFT.call("fft", a)
+def _rfft(a): return _FFT.call("rfft", a)
+def _irfft(a, n): return _FFT.call("irfft", a, n)
+def _fft2(a): return _FFT.call("fft2", a)
+def _rfft2(a): return _FFT.call("rfft2", a)
+def _irfft2(a, s): return _FFT.call("irfft2", a, s)
 
 
 # --------------------------------------------------------------------------
@@ -89,7 +129,7 @@ def naive_dft(v: np.ndarray) -> np.ndarray:
 def spectrum(c: np.ndarray) -> np.ndarray:
     """DFT of the generating vector, ``chat = FFT(c)`` (Sec. 4.2: circulant
     matrices are diagonalised by the Fourier matrix)."""
-    return np.fft.fft(np.asarray(c, dtype=np.float64))
+    return _fft(np.asarray(c, dtype=np.float64))
 
 
 def circulant_apply_fft(chat: np.ndarray, x: np.ndarray, transpose: bool = False):
@@ -101,10 +141,10 @@ def circulant_apply_fft(chat: np.ndarray, x: np.ndarray, transpose: bool = False
     """
     x = np.asarray(x, dtype=np.float64)
     n = x.shape[0]
-    xh = np.fft.rfft(x)                   # bins 0..n/2 of the real input
+    xh = _rfft(x)                         # bins 0..n/2 of the real input
     h = chat[: n // 2 + 1]
     h = h if transpose else np.conj(h)
-    return np.fft.irfft(h * xh, n)
+    return _irfft(h * xh, n)
 
 
 def forward_fft(chat, rows, x):
@@ -291,7 +331,7 @@ def admm_fft(c, rows, y, lam, sigma, rho, tau1=1.0, tau2=1.0, iters=100,
     bhat = 1.0 / (rho * np.abs(chat) ** 2 + sigma)
 
     def B_apply(b):
-        return np.fft.irfft(bhat[: n // 2 + 1] * np.fft.rfft(b), n)
+        return _irfft(bhat[: n // 2 + 1] * _rfft(b), n)
 
     return _admm(lambda v: circulant_apply_fft(chat, v),
                  lambda v: circulant_apply_fft(chat, v, transpose=True),
@@ -481,7 +521,7 @@ def ista_unrolled_grad_fft(c, rows, y, lam, tau, T, gx_T):
     n = chat.shape[0]
 
     def corr(b, a):
-        return np.fft.irfft(np.conj(np.fft.rfft(b)) * np.fft.rfft(a), n)
+        return _irfft(np.conj(_rfft(b)) * _rfft(a), n)
 
     return _ista_grad(lambda v: circulant_apply_fft(chat, v), lambda v: circulant_apply_fft(chat, v, True),
                       corr, n, rows, y, lam, tau, T, gx_T)
@@ -531,16 +571,16 @@ def naive_dft2(v: np.ndarray) -> np.ndarray:
 
 def spectrum2d(c2: np.ndarray) -> np.ndarray:
     """2D DFT of the generating array: the eigenvalues of H (conjugated)."""
-    return np.fft.fft2(np.asarray(c2, dtype=np.float64))
+    return _fft2(np.asarray(c2, dtype=np.float64))
 
 
 def circulant2d_apply_fft(chat2, x, transpose=False):
     """H x (or H^T x) of a flattened image by the 2D convolution theorem."""
     n0, n1 = chat2.shape
-    xh = np.fft.rfft2(np.asarray(x, dtype=np.float64).reshape(n0, n1))
+    xh = _rfft2(np.asarray(x, dtype=np.float64).reshape(n0, n1))
     h = chat2[:, : n1 // 2 + 1]
     h = h if transpose else np.conj(h)
-    return np.fft.irfft2(h * xh, (n0, n1)).ravel()
+    return _irfft2(h * xh, (n0, n1)).ravel()
 
 
 def forward2d_fft(chat2, pix, x):
@@ -591,7 +631,7 @@ def admm_fft2d(c2, pix, y, lam, sigma, rho, tau1=1.0, tau2=1.0, iters=100, state
     bhat = 1.0 / (rho * np.abs(chat2) ** 2 + sigma)
 
     def B_apply(b):
-        return np.fft.irfft2(bhat[:, : n1 // 2 + 1] * np.fft.rfft2(b.reshape(n0, n1)), (n0, n1)).ravel()
+        return _irfft2(bhat[:, : n1 // 2 + 1] * _rfft2(b.reshape(n0, n1)), (n0, n1)).ravel()
 
     return _admm(lambda v: circulant2d_apply_fft(chat2, v), lambda v: circulant2d_apply_fft(chat2, v, True),
                  B_apply, n0 * n1, pix, np.asarray(y, dtype=np.float64), lam, sigma, rho, tau1, tau2, iters,

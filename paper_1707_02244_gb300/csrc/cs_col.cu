@@ -63,6 +63,20 @@ template <> struct ColShape<3> {
   __device__ static constexpr int lgN2(const Geo&) { return 12; }
 };
 
+// Global source / sink of the tile's first and last FFT stages (static
+// shapes): element (column c, row j2) of the tile is W[col0 + c + j2 N1].
+struct ColIO {
+  static constexpr bool kGlobal = true;
+  float2* W;
+  int col0, lgN1;
+  __device__ __forceinline__ float2 load(int c, int j2) const {
+    return __ldcg(W + col0 + c + ((size_t)j2 << lgN1));
+  }
+  __device__ __forceinline__ void store(int c, int j2, float2 v) const {
+    __stcg(W + col0 + c + ((size_t)j2 << lgN1), v);
+  }
+};
+
 template <int SHAPE> struct ColTile {
   static constexpr int kTile = SHAPE == 3 ? COL_TILE4 : COL_TILE;
   static constexpr int kMinB = SHAPE == 3 ? COL_MINB4 : COL_MINB;
@@ -111,7 +125,11 @@ __global__ void __launch_bounds__(ColTile<SHAPE>::kTile / EPT, ColTile<SHAPE>::k
   acc.spref = spref;
   acc.wbase = wbase;
 
-  if (E::kRead) {
+  if constexpr (E::kRead && SHAPE != 0) {
+    // static shapes: the first inverse stage reads the exchange buffer itself
+    EpiHook<KIND> hook{kp, a, col0, g.lgN1, acc, col0 << lgN2, lgG};
+    tile_fft<+1, TILE, NT, TWS>(sm, lay, tw, lgN2, hook, ColIO{W, col0, g.lgN1}, SmemIO{});
+  } else if constexpr (E::kRead) {
     float4 buf[NLD];
 #pragma unroll
     for (int i = 0; i < NLD; ++i) {
@@ -151,7 +169,11 @@ __global__ void __launch_bounds__(ColTile<SHAPE>::kTile / EPT, ColTile<SHAPE>::k
         : 0;
     if (kSlots) block_stats<kSlots, NT>(acc, kp.pp.partials);
   }
-  if (E::kFwd) {
+  if constexpr (E::kFwd && SHAPE != 0) {
+    // static shapes: the last forward stage writes the exchange buffer itself
+    NoHook nh;
+    tile_fft<-1, TILE, NT, TWS>(sm, lay, tw, lgN2, nh, SmemIO{}, ColIO{W, col0, g.lgN1});
+  } else if constexpr (E::kFwd) {
     tile_fft<-1, TILE, NT, TWS>(sm, lay, tw, lgN2);
 #pragma unroll
     for (int i = 0; i < NLD; ++i) {

@@ -164,16 +164,83 @@ struct NoHook {
   __device__ __forceinline__ float2 post(int, int, int, int, float2 v) { return v; }
 };
 
+// Where a stage takes its inputs from and puts its outputs.  SmemIO (the
+// default) is the padded tile in shared memory.  A pass kernel may give the
+// first stage of an FFT a source in global memory (load(vec, idx)) and the
+// last stage a sink in global memory (store(vec, idx, v)), so that the tile
+// is never staged through shared memory on its way in or out: one shared
+// round trip and one barrier less at each end.
+struct SmemIO {
+  static constexpr bool kGlobal = false;
+  __device__ __forceinline__ float2 load(int, int) const { return make_float2(0.f, 0.f); }
+  __device__ __forceinline__ void store(int, int, float2) const {}
+};
+
+// Multiply the R inputs of a butterfly by w^(r k), r = 1 .. R-1, from the
+// stage-major table block tw[(r - 1) Ls + k] = w^(r k) in shared memory.
+// Radix 16 reads r = 1, 2, 3, 4, 8, 12 and forms the other nine as
+// w^((r1 + 4 r2) k) = w^(r1 k) w^(4 r2 k); radix 8 reads r = 1 .. 4 and forms
+// r = 5 .. 7 as w^(4k) w^((r - 4) k).  Every table value is an FP64 result
+// rounded once, so each twiddle is at most one product away from it; the
+// shared-memory reads drop from 15 to 6 (radix 16) and from 7 to 4 (radix 8).
+template <int R, int DIR>
+__device__ __forceinline__ void stage_twiddle(float2* v, const float2* __restrict__ tw, int Ls, int k) {
+  auto get = [&](int r) {
+    float2 w = tw[(r - 1) * Ls + k];
+    if (DIR > 0) w.y = -w.y;
+    return w;
+  };
+  if constexpr (R == 16) {
+    const float2 w1 = get(1), w2 = get(2), w3 = get(3);
+    const float2 w4 = get(4), w8 = get(8), w12 = get(12);
+    v[1] = cmul(v[1], w1);
+    v[2] = cmul(v[2], w2);
+    v[3] = cmul(v[3], w3);
+    v[4] = cmul(v[4], w4);
+    v[5] = cmul(v[5], cmul(w4, w1));
+    v[6] = cmul(v[6], cmul(w4, w2));
+    v[7] = cmul(v[7], cmul(w4, w3));
+    v[8] = cmul(v[8], w8);
+    v[9] = cmul(v[9], cmul(w8, w1));
+    v[10] = cmul(v[10], cmul(w8, w2));
+    v[11] = cmul(v[11], cmul(w8, w3));
+    v[12] = cmul(v[12], w12);
+    v[13] = cmul(v[13], cmul(w12, w1));
+    v[14] = cmul(v[14], cmul(w12, w2));
+    v[15] = cmul(v[15], cmul(w12, w3));
+  } else if constexpr (R == 8) {
+    const float2 w1 = get(1), w2 = get(2), w3 = get(3), w4 = get(4);
+    v[1] = cmul(v[1], w1);
+    v[2] = cmul(v[2], w2);
+    v[3] = cmul(v[3], w3);
+    v[4] = cmul(v[4], w4);
+    v[5] = cmul(v[5], cmul(w4, w1));
+    v[6] = cmul(v[6], cmul(w4, w2));
+    v[7] = cmul(v[7], cmul(w4, w3));
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], get(r));
+  }
+}
+
 // One Stockham stage of radix R over all vectors of the tile.
 //   Ls   product of the radices of the stages already done
 //   tw   without TWS: table tw[q] = exp(-2 pi i q / Lt), Lt = 1 << lgLt >= L,
 //        in global memory (read-only path).  With TWS: this stage's block of
 //        the stage-major table in shared memory, tw[(r-1) Ls + k] =
-//        w_{Ls R}^(r k), so the R-1 reads of a butterfly use immediate offsets
+//        w_{Ls R}^(r k), so the reads of a butterfly use immediate offsets
 //        and neighbouring threads read neighbouring words.
-template <int R, int DIR, int TILE, int NT, bool TWS, class LAY, class H>
+//   in   source of the stage's inputs (first stage only; SmemIO = the tile)
+//   out  sink of its outputs (last stage only; SmemIO = the tile)
+// A stage whose source is the tile waits at a barrier after reading it (the
+// tile is then overwritten); one whose sink is the tile ends with a barrier.
+// A stage with a global source must only follow a barrier after any earlier
+// use of the tile, and one with a global sink leaves the tile free for reuse
+// only after the caller's next barrier.
+template <int R, int DIR, int TILE, int NT, bool TWS, class LAY, class H, class IN = SmemIO, class OUT = SmemIO>
 __device__ __forceinline__ void stockham_stage(float2* s, const LAY& lay, int lgLs,
-                                               const float2* __restrict__ tw, int lgLt, H& hook) {
+                                               const float2* __restrict__ tw, int lgLt, H& hook,
+                                               const IN& in = IN{}, const OUT& out = OUT{}) {
   constexpr int BPT = TILE / (R * NT);   // butterflies per thread
   constexpr int lgR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
   const int lgL = lay.LG();
@@ -192,7 +259,10 @@ __device__ __forceinline__ void stockham_stage(float2* s, const LAY& lay, int lg
     if (lay.VF()) { vecs[i] = b & ((1 << lgnv) - 1); js[i] = b >> lgnv; }
     else { vecs[i] = b >> lgLR; js[i] = b & ((1 << lgLR) - 1); }
     if (b < nb) {
-      if constexpr (LAY::kStatic) {
+      if constexpr (IN::kGlobal) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i][r] = in.load(vecs[i], js[i] + (r << lgLR));
+      } else if constexpr (LAY::kStatic) {
         const float2* lb = s + LAY::padV(vecs[i]) + LAY::padP(js[i]);
 #pragma unroll
         for (int r = 0; r < R; ++r) v[i][r] = lb[LAY::padP(r << lgLR)];
@@ -202,7 +272,7 @@ __device__ __forceinline__ void stockham_stage(float2* s, const LAY& lay, int lg
       }
     }
   }
-  __syncthreads();
+  if constexpr (!IN::kGlobal) __syncthreads();
 #pragma unroll
   for (int i = 0; i < BPT; ++i) {
     const int b = threadIdx.x + i * NT;
@@ -215,12 +285,16 @@ __device__ __forceinline__ void stockham_stage(float2* s, const LAY& lay, int lg
         for (int r = 0; r < R; ++r) v[i][r] = hook.pre(vecs[i], j, r, lgLR, v[i][r]);
       }
       if (!first) {
-        const int kk = k << lgstep;   // w_{Ls R}^(r k) = tw[r * kk]
+        if constexpr (TWS) {
+          stage_twiddle<R, DIR>(v[i], tw, Ls, k);
+        } else {
+          const int kk = k << lgstep;   // w_{Ls R}^(r k) = tw[r * kk]
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = TWS ? tw[(r - 1) * Ls + k] : __ldg(tw + r * kk);
-          if (DIR > 0) w.y = -w.y;
-          v[i][r] = cmul(v[i][r], w);
+          for (int r = 1; r < R; ++r) {
+            float2 w = __ldg(tw + r * kk);
+            if (DIR > 0) w.y = -w.y;
+            v[i][r] = cmul(v[i][r], w);
+          }
         }
       }
       dft<R, DIR>(v[i]);
@@ -234,35 +308,48 @@ __device__ __forceinline__ void stockham_stage(float2* s, const LAY& lay, int lg
       for (int r = 0; r < R; ++r) {
         float2 o = v[i][out_slot<R>(r)];
         if (H::kPost && last) o = hook.post(vecs[i], j, r, lgLR, o);
-        if constexpr (LAY::kStatic) sb[LAY::padP(r * Ls)] = o;
+        if constexpr (OUT::kGlobal) out.store(vecs[i], base + r * Ls, o);
+        else if constexpr (LAY::kStatic) sb[LAY::padP(r * Ls)] = o;
         else s[pad(lay.at(vecs[i], base + r * Ls))] = o;
       }
     }
   }
-  __syncthreads();
+  if constexpr (!OUT::kGlobal) __syncthreads();
 }
 
-// Full FFT of every vector in the tile (in place, natural order in and out).
-// Forward (DIR = -1): X_k = sum_j x_j exp(-2 pi i jk/L); inverse (DIR = +1)
-// uses exp(+2 pi i jk/L) without the 1/L factor.
-template <int DIR, int TILE, int NT, bool TWS = false, class LAY, class H>
+// Full FFT of every vector in the tile (natural order in and out).  Forward
+// (DIR = -1): X_k = sum_j x_j exp(-2 pi i jk/L); inverse (DIR = +1) uses
+// exp(+2 pi i jk/L) without the 1/L factor.  The first stage reads from `in`
+// and the last writes to `out` (both the tile unless a pass gives global
+// ones; only static layouts take global ones).
+template <int DIR, int TILE, int NT, bool TWS = false, class LAY, class H, class IN = SmemIO, class OUT = SmemIO>
 __device__ __forceinline__ void tile_fft(float2* s, const LAY& lay, const float2* __restrict__ tw, int lgLt,
-                                         H& hook) {
+                                         H& hook, const IN& in = IN{}, const OUT& out = OUT{}) {
   if constexpr (LAY::kStatic) {
     constexpr int LGL = LAY::kLgL;
+    constexpr int N16 = LGL / 4;      // radix-16 stages
+    constexpr int rem = LGL % 4;      // radix of the closing stage: 2^rem (none when 0)
+    constexpr int NST = N16 + (rem ? 1 : 0);
+    static_assert(NST >= 2, "a global source and sink need distinct first and last stages");
     // with TWS, stage st (span 16^st) reads block st-1 of the stage-major table
     int off = 0;
 #pragma unroll
-    for (int st = 0; st < LGL / 4; ++st) {
-      stockham_stage<16, DIR, TILE, NT, TWS>(s, lay, 4 * st, TWS ? tw + off : tw, lgLt, hook);
+    for (int st = 0; st < N16; ++st) {
+      const float2* tws = TWS ? tw + off : tw;
+      if (st == 0)
+        stockham_stage<16, DIR, TILE, NT, TWS>(s, lay, 0, tws, lgLt, hook, in, SmemIO{});
+      else if (st == NST - 1)
+        stockham_stage<16, DIR, TILE, NT, TWS>(s, lay, 4 * st, tws, lgLt, hook, SmemIO{}, out);
+      else
+        stockham_stage<16, DIR, TILE, NT, TWS>(s, lay, 4 * st, tws, lgLt, hook);
       if (st > 0) off += 15 << (4 * st);
     }
-    constexpr int rem = LGL % 4;
     const float2* twr = TWS ? tw + off : tw;
-    if constexpr (rem == 3) stockham_stage<8, DIR, TILE, NT, TWS>(s, lay, LGL - 3, twr, lgLt, hook);
-    if constexpr (rem == 2) stockham_stage<4, DIR, TILE, NT, TWS>(s, lay, LGL - 2, twr, lgLt, hook);
-    if constexpr (rem == 1) stockham_stage<2, DIR, TILE, NT, TWS>(s, lay, LGL - 1, twr, lgLt, hook);
+    if constexpr (rem == 3) stockham_stage<8, DIR, TILE, NT, TWS>(s, lay, LGL - 3, twr, lgLt, hook, SmemIO{}, out);
+    if constexpr (rem == 2) stockham_stage<4, DIR, TILE, NT, TWS>(s, lay, LGL - 2, twr, lgLt, hook, SmemIO{}, out);
+    if constexpr (rem == 1) stockham_stage<2, DIR, TILE, NT, TWS>(s, lay, LGL - 1, twr, lgLt, hook, SmemIO{}, out);
   } else {
+    static_assert(!IN::kGlobal && !OUT::kGlobal, "run-time layouts use the shared tile only");
     int lgLs = 0;
     const int lgL = lay.LG();
     while (lgL - lgLs >= 4) { stockham_stage<16, DIR, TILE, NT, TWS>(s, lay, lgLs, tw, lgLt, hook); lgLs += 4; }
@@ -273,6 +360,7 @@ __device__ __forceinline__ void tile_fft(float2* s, const LAY& lay, const float2
   }
 }
 
+// Without element hooks (a pass that gives global ends passes a NoHook).
 template <int DIR, int TILE, int NT, bool TWS = false, class LAY>
 __device__ __forceinline__ void tile_fft(float2* s, const LAY& lay, const float2* __restrict__ tw, int lgLt) {
   NoHook h;

@@ -19,6 +19,22 @@ __device__ __forceinline__ int slot_row(const Geo& g, int u, int second) {
   return second ? g.N2 - u : u;
 }
 
+// Global source / sink of the first forward and last inverse FFT stages of
+// the static shapes: row `vec` of the tile is row slot_row(u0 + vec/2,
+// vec & 1) of the N2 x N1 exchange array.
+struct MidIO {
+  static constexpr bool kGlobal = true;
+  float2* W;
+  int u0, lgN1, N2;
+  __device__ __forceinline__ float2* at(int vec, int idx) const {
+    const int u = u0 + (vec >> 1);
+    const int k2 = u == 0 ? ((vec & 1) ? (N2 >> 1) : 0) : ((vec & 1) ? N2 - u : u);
+    return W + ((size_t)k2 << lgN1) + idx;
+  }
+  __device__ __forceinline__ float2 load(int vec, int idx) const { return __ldcg(at(vec, idx)); }
+  __device__ __forceinline__ void store(int vec, int idx, float2 v) const { __stcg(at(vec, idx), v); }
+};
+
 // Four-step twiddle as FFT hooks: w_N^(j1 k2) on the values the first
 // forward stage loads, its conjugate on the values the last inverse stage
 // produces (k2 = the tile row's index in the N2 x N1 array).  With
@@ -219,6 +235,21 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
     }
     __syncthreads();
   };
+  // static shapes: the first forward stage reads the rows from W itself
+  // (after a barrier: its hook reads the twiddle tables written above)
+  auto fwd_rows_from_global = [&]() {
+    if constexpr (TWS) {
+      __syncthreads();
+      const MidIO io{W, u0, lgN1, g.N2};
+      if constexpr (TWOD) {
+        NoHook nh;
+        tile_fft<-1, TILE, NT, true>(sm, lay, tws, lgN1, nh, io, SmemIO{});
+      } else {
+        MidTwHookS<true> h{lohi, lohi + ROWS * 16, LGN1S, make_float2(1.f, 0.f)};
+        tile_fft<-1, TILE, NT, true>(sm, lay, tws, lgN1, h, io, SmemIO{});
+      }
+    }
+  };
   auto fwd_rows = [&](float2* buf) {
     if constexpr (TWOD) {
       if constexpr (TWS) tile_fft<-1, TILE, NT, true>(buf, lay, tws, lgN1);
@@ -334,8 +365,12 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
     }
     __syncthreads();
   } else {
-    load_tile(sm, W);
-    fwd_rows(sm);
+    if constexpr (TWS) {
+      fwd_rows_from_global();
+    } else {
+      load_tile(sm, W);
+      fwd_rows(sm);
+    }
     // spectrum operator over all (k, N-k) pairs held by this CTA (unrolled so
     // that the table loads of several slots are in flight together)
 #pragma unroll 4
@@ -354,15 +389,24 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
     }
     __syncthreads();
   }
-  if constexpr (TWOD) {
-    if constexpr (TWS) tile_fft<+1, TILE, NT, true>(sm, lay, tws, lgN1);
-    else tile_fft<+1, TILE, NT, false>(sm, lay, g.tw1h, lgN1);
-  } else if constexpr (TWS) {
-    MidTwHookS<false> h{lohi, lohi + ROWS * 16, LGN1S, make_float2(1.f, 0.f)};
-    tile_fft<+1, TILE, NT, true>(sm, lay, tws, lgN1, h);
+  if constexpr (TWS) {
+    // static shapes: the last inverse stage writes the rows to W itself
+    const MidIO io{W, u0, lgN1, g.N2};
+    if constexpr (TWOD) {
+      NoHook nh;
+      tile_fft<+1, TILE, NT, true>(sm, lay, tws, lgN1, nh, SmemIO{}, io);
+    } else {
+      MidTwHookS<false> h{lohi, lohi + ROWS * 16, LGN1S, make_float2(1.f, 0.f)};
+      tile_fft<+1, TILE, NT, true>(sm, lay, tws, lgN1, h, SmemIO{}, io);
+    }
+    return;
   } else {
-    MidTwHook<false> h{g, u0, rt[1], make_float2(1.f, 0.f)};
-    tile_fft<+1, TILE, NT, false>(sm, lay, g.tw1, lgN1 + 1, h);
+    if constexpr (TWOD) {
+      tile_fft<+1, TILE, NT, false>(sm, lay, g.tw1h, lgN1);
+    } else {
+      MidTwHook<false> h{g, u0, rt[1], make_float2(1.f, 0.f)};
+      tile_fft<+1, TILE, NT, false>(sm, lay, g.tw1, lgN1 + 1, h);
+    }
   }
 
 #pragma unroll

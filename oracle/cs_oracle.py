@@ -43,7 +43,7 @@ __all__ = [
     "ista_unrolled_grad_dense", "ista_unrolled_grad_fft", "ista_unrolled_loss",
     "circulant2d_matrix", "sensing2d_matrix", "spectrum2d", "circulant2d_apply_fft", "forward2d_fft",
     "adjoint2d_fft", "ista_dense2d", "ista_fft2d", "admm_dense2d", "admm_fft2d", "naive_dft2",
-    "set_fft_threads",
+    "set_fft_threads", "admm_unrolled_grad_dense", "admm_unrolled_grad_fft", "admm_unrolled_loss",
 ]
 
 
@@ -470,7 +470,7 @@ def l0_bruteforce(A, y, kmax, tol=1e-9):
 # the last from dC/dc_k = Pi_k, (Pi_k)_{ij} = 1 if (j - i) mod n == k, so that
 # w^T du/dc_k = tau ((Pi_k w)^T r - (M C w)^T (Pi_k x)).
 
-def _ista_grad(C_apply, Ct_apply, corr, n, rows, y, lam, tau, T, gx_T):
+def _ista_grad(C_apply, Ct_apply, corr, n, rows, y, lam, tau, T, gx_T, active=None):
     rows = np.asarray(rows, dtype=np.int64)
     y = np.asarray(y, dtype=np.float64)
     theta = tau * lam
@@ -490,7 +490,8 @@ def _ista_grad(C_apply, Ct_apply, corr, n, rows, y, lam, tau, T, gx_T):
     dy = np.zeros(len(rows))
     for t in range(T - 1, -1, -1):
         x, u = xs[t], us[t]
-        w = np.where(np.abs(u) > theta, g, 0.0)
+        on = np.abs(u) > theta if active is None else np.asarray(active(t), dtype=bool)
+        w = np.where(on, g, 0.0)
         dtheta -= float(np.sum(np.sign(u) * w))
         cw = C_apply(w)
         q = mask * cw
@@ -514,9 +515,16 @@ def ista_unrolled_grad_dense(c, rows, y, lam, tau, T, gx_T):
     return _ista_grad(lambda v: C @ v, lambda v: C.T @ v, corr, n, rows, y, lam, tau, T, gx_T)
 
 
-def ista_unrolled_grad_fft(c, rows, y, lam, tau, T, gx_T):
+def ista_unrolled_grad_fft(c, rows, y, lam, tau, T, gx_T, active=None):
     """As ista_unrolled_grad_dense with the products and correlations taken
-    by FFT: DFT(sum_i b_i a_{i+k}) = conj(DFT b) DFT a for real a, b."""
+    by FFT: DFT(sum_i b_i a_{i+k}) = conj(DFT b) DFT a for real a, b.
+
+    ``active``: optional callable, active(t) = the boolean set on which step
+    t's soft threshold passes its input (x(t+1) != 0) of some other forward
+    trajectory, used in place of this trajectory's {|u(t)| > theta}.  The
+    reverse pass is then the derivative along that trajectory's supports (an
+    analysis aid: it separates the effect of support differences between two
+    forward passes from the rest)."""
     chat = spectrum(c)
     n = chat.shape[0]
 
@@ -524,7 +532,7 @@ def ista_unrolled_grad_fft(c, rows, y, lam, tau, T, gx_T):
         return _irfft(np.conj(_rfft(b)) * _rfft(a), n)
 
     return _ista_grad(lambda v: circulant_apply_fft(chat, v), lambda v: circulant_apply_fft(chat, v, True),
-                      corr, n, rows, y, lam, tau, T, gx_T)
+                      corr, n, rows, y, lam, tau, T, gx_T, active)
 
 
 def ista_unrolled_loss(c, rows, y, lam, tau, T, x_star, dense=True):
@@ -533,6 +541,135 @@ def ista_unrolled_loss(c, rows, y, lam, tau, T, x_star, dense=True):
     xT = run(c, rows, y, lam, tau, T)
     d = xT - np.asarray(x_star, dtype=np.float64)
     return float(np.dot(d, d)), 2.0 * d
+
+
+# --------------------------------------------------------------------------
+# Reverse mode of unrolled circulant ADMM (no counterpart in the paper: the
+# derivative of T iterations of Algorithm 3, from the zero state, with
+# respect to c, lambda and y)
+# --------------------------------------------------------------------------
+#
+# One iteration maps the state (v, z, mu, nu) -- v the folded v + mu of the
+# loop's last line -- to (v2, z1, mu1, nu1):
+#   b  = rho C^T v + sigma (z - nu),   x = B b,   B = (rho C^T C + sigma I)^-1
+#   p  = C x,   v1 = D (rho p - rho mu + P^T y)
+#   s  = x + nu,   z1 = eta_theta(s),   theta = lam / sigma
+#   mu1 = mu + tau1 (v1 - p),   nu1 = nu + tau2 (x - z1),   v2 = v1 + mu1.
+# Given the adjoints (v2', z1', mu1', nu1') of the new state (primes denote
+# dL/d.), the chain rule gives, in this order,
+#   mu1' += v2';  v1' = v2' + tau1 mu1';  p' = -tau1 mu1'
+#   x' = tau2 nu1';  z1' -= tau2 nu1';  nu' = nu1'
+#   s' = z1' on {|s| > theta} (0 elsewhere, |s| == theta included);
+#   lam' += -(1/sigma) sum sign(s) s';  x' += s';  nu' += s'
+#   a' = D v1';  p' += rho a';  mu' = mu1' - rho a';  y' += P a'
+#   x' += C^T p';  c'_k += sum_i p'_i x_{i+k}
+#   b' = B x';  c'_k -= rho (sum_i p_i b'_{i+k} + sum_i (C b')_i x_{i+k})
+#   v' = rho C b';  c'_k += rho sum_i v_i b'_{i+k};  z' = sigma b';  nu' -= sigma b'
+# (indices mod n).  The c-terms come from dC/dc_k = Pi_k, (Pi_k u)_i =
+# u_{i+k}: p = C x gives p'^T Pi_k x; C^T v gives b'^T Pi_k^T v; and
+# dB = -B dM B with dM = rho (dC^T C + C^T dC) gives -b'^T dM x.  D depends on
+# rho alone.  The loss may depend on z(T) and x(T) of the last iteration.
+
+def _admm_grad(C_apply, Ct_apply, B_apply, corr, n, rows, y, lam, sigma, rho, tau1, tau2, T, gz_T,
+               gx_T=None):
+    rows = np.asarray(rows, dtype=np.int64)
+    y = np.asarray(y, dtype=np.float64)
+    theta = lam / sigma
+    d = admm_d_diagonal(n, rows, rho)
+    pty = zero_fill(n, rows, y)
+    v = np.zeros(n); z = np.zeros(n); mu = np.zeros(n); nu = np.zeros(n)
+    steps = []
+    for _ in range(T):
+        x = B_apply(rho * Ct_apply(v) + sigma * (z - nu))
+        p = C_apply(x)
+        v1 = d * (rho * p - rho * mu + pty)
+        s = x + nu
+        z1 = soft_threshold(s, theta)
+        mu1 = mu + tau1 * (v1 - p)
+        nu1 = nu + tau2 * (x - z1)
+        steps.append((v, x, p, s))
+        v, z, mu, nu = v1 + mu1, z1, mu1, nu1
+    out = {"x_T": steps[-1][1], "z_T": z}
+    vb = np.zeros(n)
+    zb = np.asarray(gz_T, dtype=np.float64).copy()
+    mub = np.zeros(n)
+    nub = np.zeros(n)
+    dc = np.zeros(n)
+    dlam = 0.0
+    dy = np.zeros(len(rows))
+    for t in range(T - 1, -1, -1):
+        v0, x, p, s = steps[t]
+        mub = mub + vb
+        v1b = vb + tau1 * mub
+        pb = -tau1 * mub
+        xb = tau2 * nub
+        if t == T - 1 and gx_T is not None:
+            xb = xb + np.asarray(gx_T, dtype=np.float64)
+        zb = zb - tau2 * nub
+        sb = np.where(np.abs(s) > theta, zb, 0.0)
+        dlam -= float(np.sum(np.sign(s) * sb)) / sigma
+        xb = xb + sb
+        nub = nub + sb
+        ab = d * v1b
+        pb = pb + rho * ab
+        mub = mub - rho * ab
+        dy += ab[rows]
+        xb = xb + Ct_apply(pb)
+        dc += corr(pb, x)
+        bb = B_apply(xb)
+        cbb = C_apply(bb)
+        dc -= rho * (corr(p, bb) + corr(cbb, x))
+        dc += rho * corr(v0, bb)
+        vb = rho * cbb
+        zb = sigma * bb
+        nub = nub - sigma * bb
+    out.update({"dc": dc, "dlam": dlam, "dy": dy})
+    return out
+
+
+def admm_unrolled_grad_dense(c, rows, y, lam, sigma, rho, tau1, tau2, T, gz_T, gx_T=None):
+    """Gradient of a loss L(z(T), x(T)) of T iterations of Algorithm 3 from
+    the zero state with respect to c, lam and y, given gz_T = dL/dz(T) (and
+    gx_T = dL/dx(T), optional).  Dense C, B by a dense Cholesky factor; the
+    correlation sum_i b_i a_{(i+k) mod n} is formed for every k by rolling a."""
+    C = circulant_matrix(c)
+    n = C.shape[0]
+    L = np.linalg.cholesky(rho * (C.T @ C) + sigma * np.eye(n))
+
+    def B_apply(b):
+        return np.linalg.solve(L.T, np.linalg.solve(L, b))
+
+    def corr(b, a):
+        return np.array([np.dot(b, np.roll(a, -k)) for k in range(n)])
+
+    return _admm_grad(lambda v: C @ v, lambda v: C.T @ v, B_apply, corr, n, rows, y, lam, sigma, rho, tau1, tau2,
+                      T, gz_T, gx_T)
+
+
+def admm_unrolled_grad_fft(c, rows, y, lam, sigma, rho, tau1, tau2, T, gz_T, gx_T=None):
+    """As admm_unrolled_grad_dense with products, the circulant inverse B and
+    the correlations taken by FFT."""
+    chat = spectrum(c)
+    n = chat.shape[0]
+    bhat = 1.0 / (rho * np.abs(chat) ** 2 + sigma)
+
+    def B_apply(b):
+        return _irfft(bhat[: n // 2 + 1] * _rfft(b), n)
+
+    def corr(b, a):
+        return _irfft(np.conj(_rfft(b)) * _rfft(a), n)
+
+    return _admm_grad(lambda v: circulant_apply_fft(chat, v), lambda v: circulant_apply_fft(chat, v, True),
+                      B_apply, corr, n, rows, y, lam, sigma, rho, tau1, tau2, T, gz_T, gx_T)
+
+
+def admm_unrolled_loss(c, rows, y, lam, sigma, rho, tau1, tau2, T, x_star, dense=True):
+    """L = ||z(T) - x*||^2 after T iterations of Algorithm 3 from the zero
+    state, and dL/dz(T)."""
+    run = admm_dense if dense else admm_fft
+    zT = run(c, rows, y, lam, sigma=sigma, rho=rho, tau1=tau1, tau2=tau2, iters=T)["z"]
+    dz = zT - np.asarray(x_star, dtype=np.float64)
+    return float(np.dot(dz, dz)), 2.0 * dz
 
 
 # --------------------------------------------------------------------------

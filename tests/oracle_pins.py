@@ -355,6 +355,39 @@ def check_unrolled_grad_finite_differences(O):
     assert np.allclose(gr["x_T"], O.ista_dense(inst.c, inst.rows, y, lam, tau, T), atol=1e-14)
 
 
+def check_unrolled_grad_active_override(O):
+    """Handing the reverse mode the forward pass's own supports (x(t+1) != 0)
+    reproduces the default result exactly; handing it the supports with one
+    entry removed changes dy (so the override is really used)."""
+    inst = synth.instance(256, 96, k=6, noise_std=1e-3, seed=8123)
+    chat = O.spectrum(inst.c)
+    y = O.forward_fft(chat, inst.rows, inst.x_true) + inst.noise
+    tau = 0.9 / float(np.max(np.abs(chat) ** 2))
+    lam, T = 2e-3, 12
+    xs = [np.zeros(inst.n)]
+    for _ in range(T):
+        xs.append(O.ista_fft(inst.c, inst.rows, y, lam, tau, 1, x0=xs[-1]))
+    gx = 2.0 * (xs[-1] - inst.x_true)
+    base = O.ista_unrolled_grad_fft(inst.c, inst.rows, y, lam, tau, T, gx)
+    same = O.ista_unrolled_grad_fft(inst.c, inst.rows, y, lam, tau, T, gx, active=lambda t: xs[t + 1] != 0)
+    for key in ("dc", "dy", "dx0"):
+        assert np.array_equal(base[key], same[key]), key
+    assert base["dlam"] == same["dlam"]
+    t0 = T - 1
+    on = np.flatnonzero(xs[t0 + 1])
+    assert on.size > 0
+
+    def fewer(t):
+        a = xs[t + 1] != 0
+        if t == t0:
+            a = a.copy()
+            a[on[0]] = False
+        return a
+
+    other = O.ista_unrolled_grad_fft(inst.c, inst.rows, y, lam, tau, T, gx, active=fewer)
+    assert not np.allclose(other["dy"], base["dy"], rtol=1e-9, atol=0.0)
+
+
 def check_unrolled_grad_dense_fft_agree(O):
     """Dense and FFT forms of the gradient agree to rounding, and the FFT
     form also matches central differences at a larger size."""
@@ -373,6 +406,72 @@ def check_unrolled_grad_dense_fft_agree(O):
     lm = O.ista_unrolled_loss(inst.c - h * d, inst.rows, y, lam, tau, T, inst.x_true, dense=False)[0]
     fd = (lp - lm) / (2 * h)
     assert abs(fd - float(np.dot(gf["dc"], d))) <= 1e-6 * max(1.0, abs(fd))
+
+
+def _smooth_admm_instance(O, n, m, k, T, sigma, rho, tau1, tau2, seed0, margin=1e-4):
+    """A seeded instance whose T ADMM iterations keep every |x + nu| at least
+    `margin` away from the threshold lam / sigma (central differences with a
+    much smaller step then never cross a kink of the soft threshold)."""
+    for seed in range(seed0, seed0 + 50):
+        inst = synth.instance(n, m, k=k, noise_std=1e-2, seed=seed)
+        A = O.sensing_matrix(inst.c, inst.rows)
+        y = A @ inst.x_true + inst.noise
+        lam = 0.05 * float(np.max(np.abs(A.T @ y)))
+        gap, nz = np.inf, 0
+        for t in range(1, T + 1):
+            st = O.admm_dense(inst.c, inst.rows, y, lam, sigma, rho, tau1, tau2, iters=t)
+            prev = O.admm_dense(inst.c, inst.rows, y, lam, sigma, rho, tau1, tau2, iters=t - 1) if t > 1 else None
+            nu_in = prev["nu"] if prev is not None else np.zeros(n)
+            s = st["x"] + nu_in
+            gap = min(gap, float(np.min(np.abs(np.abs(s) - lam / sigma))))
+            nz = np.count_nonzero(st["z"])
+        if gap > margin and nz > 0:
+            return inst, y, lam
+    raise AssertionError("no smooth instance found")
+
+
+def check_admm_grad_finite_differences(O):
+    """The reverse-mode gradient of L = ||z(T) - x*||^2 + 0.5 ||x(T)||^2 over
+    T iterations of Algorithm 3 (general sigma, rho, tau1, tau2) equals
+    central finite differences of the forward iteration (admm_dense, pinned
+    above) along random directions in c, y and for lambda."""
+    n, m, T = 32, 14, 10
+    sg, rh, t1, t2 = 0.8, 1.3, 1.1, 0.9
+    inst, y, lam = _smooth_admm_instance(O, n, m, 3, T, sg, rh, t1, t2, 311)
+
+    def loss(c, yy, ll):
+        st = O.admm_dense(c, inst.rows, yy, ll, sg, rh, t1, t2, iters=T)
+        dz = st["z"] - inst.x_true
+        return float(dz @ dz) + 0.5 * float(st["x"] @ st["x"]), 2.0 * dz, st["x"]
+
+    _, gz, xT = loss(inst.c, y, lam)
+    gr = O.admm_unrolled_grad_dense(inst.c, inst.rows, y, lam, sg, rh, t1, t2, T, gz, gx_T=xT)
+    h = 1e-6
+    g = synth.rng(312)
+    d = g.standard_normal(n)
+    fd = (loss(inst.c + h * d, y, lam)[0] - loss(inst.c - h * d, y, lam)[0]) / (2 * h)
+    assert abs(fd - float(gr["dc"] @ d)) <= 1e-6 * max(1.0, abs(fd)), ("dc", fd, float(gr["dc"] @ d))
+    d = g.standard_normal(m)
+    fd = (loss(inst.c, y + h * d, lam)[0] - loss(inst.c, y - h * d, lam)[0]) / (2 * h)
+    assert abs(fd - float(gr["dy"] @ d)) <= 1e-6 * max(1.0, abs(fd)), ("dy", fd, float(gr["dy"] @ d))
+    fd = (loss(inst.c, y, lam + h)[0] - loss(inst.c, y, lam - h)[0]) / (2 * h)
+    assert abs(fd - gr["dlam"]) <= 1e-6 * max(1.0, abs(fd)), ("dlam", fd, gr["dlam"])
+    assert np.allclose(gr["z_T"], O.admm_dense(inst.c, inst.rows, y, lam, sg, rh, t1, t2, iters=T)["z"],
+                       atol=1e-14)
+
+
+def check_admm_grad_dense_fft_agree(O):
+    """The FFT form of the ADMM reverse mode equals the dense form."""
+    inst = synth.instance(128, 50, k=5, noise_std=1e-3, seed=321)
+    A = O.sensing_matrix(inst.c, inst.rows)
+    y = A @ inst.x_true + inst.noise
+    lam, T = 0.02 * float(np.max(np.abs(A.T @ y))), 15
+    _, gz = O.admm_unrolled_loss(inst.c, inst.rows, y, lam, 1.0, 0.7, 1.0, 1.2, T, inst.x_true)
+    a = O.admm_unrolled_grad_dense(inst.c, inst.rows, y, lam, 1.0, 0.7, 1.0, 1.2, T, gz)
+    b = O.admm_unrolled_grad_fft(inst.c, inst.rows, y, lam, 1.0, 0.7, 1.0, 1.2, T, gz)
+    for key in ("dc", "dy", "z_T"):
+        assert np.linalg.norm(a[key] - b[key]) <= 1e-11 * max(1.0, np.linalg.norm(a[key])), key
+    assert abs(a["dlam"] - b["dlam"]) <= 1e-11 * max(1.0, abs(a["dlam"]))
 
 
 def check_product_of_circulants(O):
@@ -474,6 +573,7 @@ ALL_CHECKS = [
     check_admm_fixed_point_relations, check_bruteforce_lasso,
     check_exact_recovery_tiny, check_admm_inverse, check_dense_fft_agree,
     check_opnorm, check_unrolled_grad_finite_differences, check_unrolled_grad_dense_fft_agree,
+    check_unrolled_grad_active_override, check_admm_grad_finite_differences, check_admm_grad_dense_fft_agree,
     check_2d_separable_is_kronecker, check_2d_eigenvectors, check_2d_point_source_is_psf,
     check_2d_fft_matches_dense, check_product_of_circulants,
 ]

@@ -92,7 +92,7 @@ def _admm_variant(drop_sigma=False, no_fold=False, nu_sign=+1, z_thr_rho=False):
 
 def _grad_variant(drop_q=False, active_from_x=False, dy_no_tau=False, dlam_sign=-1.0, corr_swap=False):
     """_ista_grad with one planted mistake."""
-    def _g(C_apply, Ct_apply, corr, n, rows, y, lam, tau, T, gx_T):
+    def _g(C_apply, Ct_apply, corr, n, rows, y, lam, tau, T, gx_T, active=None):
         rows = np.asarray(rows, dtype=np.int64)
         y = np.asarray(y, dtype=np.float64)
         theta = tau * lam
@@ -113,6 +113,8 @@ def _grad_variant(drop_q=False, active_from_x=False, dy_no_tau=False, dlam_sign=
         for t in range(T - 1, -1, -1):
             x, u = xs[t], us[t]
             act = (np.abs(x) > 0) if active_from_x else (np.abs(u) > theta)
+            if active is not None:
+                act = np.asarray(active(t), dtype=bool)
             w = np.where(act, g, 0.0)
             dtheta += dlam_sign * float(np.sum(np.sign(u) * w))
             cw = C_apply(w)
@@ -123,6 +125,63 @@ def _grad_variant(drop_q=False, active_from_x=False, dy_no_tau=False, dlam_sign=
             dc += tau * (term - (0.0 if drop_q else corr(q, x)))
             g = w - tau * Ct_apply(q)
         return {"x_T": xs[-1], "dc": dc, "dlam": tau * dtheta, "dy": dy, "dx0": g}
+    return _g
+
+
+def _admm_grad_variant(drop_b_term=False, drop_ctv_term=False, no_d=False, mu_sign=-1.0, drop_nu_sigma=False,
+                       no_fold=False):
+    """_admm_grad with one planted mistake."""
+    def _g(C_apply, Ct_apply, B_apply, corr, n, rows, y, lam, sigma, rho, tau1, tau2, T, gz_T, gx_T=None):
+        rows = np.asarray(rows, dtype=np.int64)
+        y = np.asarray(y, dtype=np.float64)
+        theta = lam / sigma
+        d = O.admm_d_diagonal(n, rows, rho)
+        pty = O.zero_fill(n, rows, y)
+        v = np.zeros(n); z = np.zeros(n); mu = np.zeros(n); nu = np.zeros(n)
+        steps = []
+        for _ in range(T):
+            x = B_apply(rho * Ct_apply(v) + sigma * (z - nu))
+            p = C_apply(x)
+            v1 = d * (rho * p - rho * mu + pty)
+            s = x + nu
+            z1 = O.soft_threshold(s, theta)
+            mu1 = mu + tau1 * (v1 - p)
+            nu1 = nu + tau2 * (x - z1)
+            steps.append((v, x, p, s))
+            v, z, mu, nu = v1 + mu1, z1, mu1, nu1
+        vb = np.zeros(n); zb = np.asarray(gz_T, dtype=np.float64).copy(); mub = np.zeros(n); nub = np.zeros(n)
+        dc = np.zeros(n); dlam = 0.0; dy = np.zeros(len(rows))
+        for t in range(T - 1, -1, -1):
+            v0, x, p, s = steps[t]
+            if not no_fold:
+                mub = mub + vb
+            v1b = vb + tau1 * mub
+            pb = -tau1 * mub
+            xb = tau2 * nub
+            if t == T - 1 and gx_T is not None:
+                xb = xb + np.asarray(gx_T, dtype=np.float64)
+            zb = zb - tau2 * nub
+            sb = np.where(np.abs(s) > theta, zb, 0.0)
+            dlam -= float(np.sum(np.sign(s) * sb)) / sigma
+            xb = xb + sb
+            nub = nub + sb
+            ab = v1b if no_d else d * v1b
+            pb = pb + rho * ab
+            mub = mub + mu_sign * rho * ab
+            dy += ab[rows]
+            xb = xb + Ct_apply(pb)
+            dc += corr(pb, x)
+            bb = B_apply(xb)
+            cbb = C_apply(bb)
+            if not drop_b_term:
+                dc -= rho * (corr(p, bb) + corr(cbb, x))
+            if not drop_ctv_term:
+                dc += rho * corr(v0, bb)
+            vb = rho * cbb
+            zb = sigma * bb
+            if not drop_nu_sigma:
+                nub = nub - sigma * bb
+        return {"x_T": steps[-1][1], "z_T": z, "dc": dc, "dlam": dlam, "dy": dy}
     return _g
 
 
@@ -167,6 +226,12 @@ MUTANTS = {
     "grad_dy_no_tau": ("_ista_grad", _grad_variant(dy_no_tau=True)),
     "grad_dlam_sign": ("_ista_grad", _grad_variant(dlam_sign=+1.0)),
     "grad_corr_swapped": ("_ista_grad", _grad_variant(corr_swap=True)),
+    "admm_grad_drop_inverse_term": ("_admm_grad", _admm_grad_variant(drop_b_term=True)),
+    "admm_grad_drop_ctv_term": ("_admm_grad", _admm_grad_variant(drop_ctv_term=True)),
+    "admm_grad_no_d": ("_admm_grad", _admm_grad_variant(no_d=True)),
+    "admm_grad_mu_sign": ("_admm_grad", _admm_grad_variant(mu_sign=+1.0)),
+    "admm_grad_drop_nu_sigma": ("_admm_grad", _admm_grad_variant(drop_nu_sigma=True)),
+    "admm_grad_no_fold": ("_admm_grad", _admm_grad_variant(no_fold=True)),
     "c2d_transposed": ("circulant2d_matrix", _mut_circulant2d_transposed),
     "c2d_axes_mixed": ("circulant2d_matrix", _mut_circulant2d_axes_mixed),
     "c2d_fft_conj_swapped": ("circulant2d_apply_fft", _mut_c2d_apply_conj),

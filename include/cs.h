@@ -191,6 +191,29 @@ cs_status cs_plan_2d(cs_plan_t* out, int64_t n0, int64_t n1, int64_t m, const in
 cs_status cs_grad(cs_plan_t plan, const float* y, float lambda, float tau, int T, int K,
                   const float* gx_T, float* dc, float* dlambda, float* dy);
 
+/* Gradient of unrolled circulant ADMM (no counterpart in the paper: reverse
+ * mode through T iterations of Algorithm 3).  From the zero state, with
+ * the iteration cs_admm_ex computes for the parameters prm (sigma, rho,
+ * tau1, tau2 of Algorithm 3), and a loss L(z(T), x(T)) of the last
+ * iteration's sparse estimate z and x-update x:
+ *   gz_T    DEVICE float[n]: dL/dz(T)
+ *   gx_T    DEVICE float[n]: dL/dx(T), or NULL (L does not depend on x(T))
+ *   dc      DEVICE float[n]: dL/dc (c as given to cs_plan, natural order)
+ *   dlambda DEVICE float[1]: dL/dlambda
+ *   dy      DEVICE float[m]: dL/dy (y[i] pairs with rows[i] as given)
+ * c enters through C, C^T and the inverse B = (rho C^T C + sigma I)^-1; the
+ * soft threshold's derivative is 1 where |x + nu| > lambda / sigma and 0
+ * elsewhere.  The state entering every K-th iteration is kept (4 n floats
+ * per checkpoint); each segment of K iterations is replayed, keeping per
+ * iteration the transform of its forward pair (2 n floats) and the soft
+ * threshold's input (n floats), and then back-propagated, each iteration
+ * as one column pass and one mid pass.  Buffers are allocated by the first
+ * call and kept by the plan.  1 <= K <= T; 1D plans only (a 2D plan
+ * returns CS_ERR_UNSUPPORTED).  Asynchronous; errors as cs_admm_ex.  Uses
+ * the plan's solver state: not concurrent with cs_ista / cs_admm. */
+cs_status cs_grad_admm(cs_plan_t plan, const float* y, float lambda, const cs_admm_params* prm, int T, int K,
+                       const float* gz_T, const float* gx_T, float* dc, float* dlambda, float* dy);
+
 /* ---------------------------------------------------------------------
  * Batched solves (no counterpart in the paper; its recovery problem solved
  * for many independent instances at once).  Instance i has its own n_i,

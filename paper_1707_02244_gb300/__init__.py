@@ -26,7 +26,7 @@ EXPORTS = ("cs_plan", "cs_plan_destroy", "cs_opnorm2", "cs_forward", "cs_adjoint
            "cs_set_monitor", "cs_ista", "cs_admm", "cs_admm_ex", "cs_status_sync",
            "cs_status_string", "cs_version", "cs_profile_pass", "cs_circulant_apply_static",
            "cs_batch_plan", "cs_batch_destroy", "cs_batch_ista", "cs_batch_admm", "cs_batch_status_sync",
-           "cs_grad", "cs_forward_direct", "cs_plan_2d")
+           "cs_grad", "cs_forward_direct", "cs_plan_2d", "cs_grad_admm")
 
 
 class CsStats(ctypes.Structure):
@@ -71,6 +71,7 @@ def _load() -> ctypes.CDLL:
         "cs_profile_pass": [vp, ci, ci],
         "cs_circulant_apply_static": [i64, vp, vp, vp, ci, vp],
         "cs_grad": [vp, vp, f32, f32, ci, ci, vp, vp, vp, vp],
+        "cs_grad_admm": [vp, vp, f32, ctypes.POINTER(CsAdmmParams), ci, ci, vp, vp, vp, vp, vp],
         "cs_plan_2d": [ctypes.POINTER(vp), i64, i64, i64, vp, vp, vp],
         "cs_forward_direct": [i64, i64, vp, vp, vp, vp, vp],
         "cs_batch_plan": [ctypes.POINTER(vp), ci, vp, vp, vp, vp, vp],
@@ -231,6 +232,16 @@ def cs_grad(plan: Plan, y, lam: float, tau: float, T: int, K: int, gx_T, dc, dla
     dy receive dL/dc, dL/dlambda, dL/dy for gx_T = dL/dx(T)."""
     _check(_lib.cs_grad(plan.handle, _ptr(y), lam, tau, int(T), int(K), _ptr(gx_T), _ptr(dc), _ptr(dlam),
                         _ptr(dy)), "cs_grad")
+
+
+def cs_grad_admm(plan: Plan, y, lam: float, sigma: float, rho: float, tau1: float, tau2: float, T: int, K: int,
+                 gz_T, dc, dlam, dy, gx_T=None):
+    """Reverse mode of T iterations of Algorithm 3 from the zero state: dc,
+    dlam (1 element) and dy receive dL/dc, dL/dlambda, dL/dy for gz_T =
+    dL/dz(T) (and gx_T = dL/dx(T) when the loss also depends on x(T))."""
+    prm = CsAdmmParams(sigma, rho, tau1, tau2)
+    _check(_lib.cs_grad_admm(plan.handle, _ptr(y), lam, ctypes.byref(prm), int(T), int(K), _ptr(gz_T),
+                             _ptr(gx_T), _ptr(dc), _ptr(dlam), _ptr(dy)), "cs_grad_admm")
 
 
 def _make_unrolled_ista():

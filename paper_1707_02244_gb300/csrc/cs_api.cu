@@ -74,6 +74,20 @@ struct cs_plan_s {
     double* gpart = nullptr; // per column CTA: dL/dtheta
     CallArgs* ca = nullptr;  // [seg_cap + 1]: step j of a segment, and the output pass
   } gr;
+  // unrolled-ADMM gradient (cs_grad_admm): allocated at the first call, grown on demand
+  struct GradA {
+    int ck_cap = 0, seg_cap = 0;
+    float* ckpt = nullptr;   // [ck_cap][4][n]  state (v, z, mu, nu) entering iteration sK, tile order
+    float2* wseg = nullptr;  // [seg_cap][n]  column transform of iteration j's forward pair v + i (z - nu)
+    float* sseg = nullptr;   // [seg_cap][n]  iteration j's soft-threshold input x + nu
+    float *mub = nullptr, *nub = nullptr;   // adjoint state (mu', nu' without -sigma b')
+    float *gz = nullptr, *gx = nullptr;     // dL/dz(T), dL/dx(T) in tile order
+    float* dy = nullptr;     // [m] dL/dy, compact in the tile order of the rows
+    float2* Wr = nullptr;    // exchange buffer of the reverse pass
+    float2* gacc = nullptr;  // per pair slot: spectrum of dL/dc (over N)
+    double* gpart = nullptr; // per column CTA: sum of -sign(s) s'
+    CallArgs* ca = nullptr;  // [2 seg_cap + 2]: replay steps, reverse steps, first reverse step, output
+  } ga_;
 };
 
 namespace {
@@ -174,6 +188,10 @@ void free_plan(cs_plan_s* p) {
   void* gbufs[] = {p->gr.ckpt, p->gr.seg, p->gr.rseg, p->gr.g, p->gr.w, p->gr.q, p->gr.dy, p->gr.W2, p->gr.gacc,
                    p->gr.gpart, p->gr.ca};
   for (void* b : gbufs)
+    if (b) cudaFree(b);
+  void* abufs[] = {p->ga_.ckpt, p->ga_.wseg, p->ga_.sseg, p->ga_.mub, p->ga_.nub, p->ga_.gz, p->ga_.gx,
+                   p->ga_.dy, p->ga_.Wr, p->ga_.gacc, p->ga_.gpart, p->ga_.ca};
+  for (void* b : abufs)
     if (b) cudaFree(b);
   if (p->host_stats) cudaFreeHost(p->host_stats);
   if (p->host_status) cudaFreeHost(p->host_status);
@@ -972,3 +990,207 @@ cs_status cs_grad(cs_plan_t p, const float* y, float lambda, float tau, int T, i
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ ADMM gradient
+
+namespace {
+
+cudaError_t grad_admm_reserve(cs_plan_s* p, int ck, int seg) {
+  auto& G = p->ga_;
+  if (G.ckpt && ck <= G.ck_cap && seg <= G.seg_cap) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return e;
+  for (auto it = p->graphs.begin(); it != p->graphs.end();) {   // graphs holding the old addresses
+    if ((it->first >> 40) >= 5) {
+      cudaGraphExecDestroy(it->second);
+      it = p->graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  const int nck = ck > G.ck_cap ? ck : G.ck_cap, nseg = seg > G.seg_cap ? seg : G.seg_cap;
+  void* old[] = {G.ckpt, G.wseg, G.sseg, G.mub, G.nub, G.gz, G.gx, G.dy, G.Wr, G.gacc, G.gpart, G.ca};
+  for (void* b : old)
+    if (b) cudaFree(b);
+  G = cs_plan_s::GradA{};
+  const size_t n = (size_t)p->n;
+  e = dalloc(&G.ckpt, (size_t)nck * 4 * n);
+  if (e == cudaSuccess) e = dalloc(&G.wseg, (size_t)nseg * n);
+  if (e == cudaSuccess) e = dalloc(&G.sseg, (size_t)nseg * n);
+  for (float** b : {&G.mub, &G.nub, &G.gz, &G.gx})
+    if (e == cudaSuccess) e = dalloc(b, n);
+  if (e == cudaSuccess) e = dalloc(&G.dy, (size_t)p->m);
+  if (e == cudaSuccess) e = dalloc(&G.Wr, n);
+  if (e == cudaSuccess) e = dalloc(&G.gacc, (size_t)tab_count(p->ga));
+  if (e == cudaSuccess) e = dalloc(&G.gpart, (size_t)p->ga.col_ctas);
+  if (e == cudaSuccess) e = dalloc(&G.ca, 2 * (size_t)nseg + 2);
+  if (e == cudaSuccess) {
+    G.ck_cap = nck;
+    G.seg_cap = nseg;
+  }
+  return e;
+}
+
+// Pass parameters of the ADMM gradient: the complex-n geometry, the reverse
+// exchange buffer and accumulators, and the CallArgs entry `ca`.
+KParams kp_admm(const cs_plan_s* p, const CallArgs* ca, float2* W, const float2* W2) {
+  KParams k = kparams(p, p->ga, 0);
+  k.pp.W = W;
+  k.pp.W2 = const_cast<float2*>(W2);
+  k.pp.gacc_a = p->ga_.gacc;
+  k.pp.gpart = p->ga_.gpart;
+  k.ca = ca;
+  return k;
+}
+
+// Replay of one segment of L iterations from the state in (av, az, amu, anu):
+// iteration j keeps the column transform of its forward pair (wseg[j]) and
+// its soft-threshold input (sseg[j]).
+cudaError_t enqueue_admm_replay(cs_plan_s* p, int L, cudaStream_t s) {
+  auto& G = p->ga_;
+  const size_t n = (size_t)p->n;
+  cudaError_t e = launch_col(COL_ADMM_INIT, kp_admm(p, G.ca, p->W, nullptr), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(G.wseg, p->W, n * sizeof(float2), cudaMemcpyDeviceToDevice, s);
+  for (int j = 0; j < L && e == cudaSuccess; ++j) {
+    e = launch_mid(MID_ADMM, kp_admm(p, G.ca + j, p->W, nullptr), s);
+    if (e == cudaSuccess) e = launch_col(COL_ADMM_SEG, kp_admm(p, G.ca + j, p->W, nullptr), s);
+    if (e == cudaSuccess && j + 1 < L)
+      e = cudaMemcpyAsync(G.wseg + (j + 1) * n, p->W, n * sizeof(float2), cudaMemcpyDeviceToDevice, s);
+  }
+  return e;
+}
+
+// Reverse of iterations L-1 .. 0 of one segment; `first`: the segment that
+// ends at iteration T (its last iteration takes dL/dz(T), dL/dx(T)).
+cudaError_t enqueue_admm_reverse(cs_plan_s* p, int L, bool first, cudaStream_t s) {
+  auto& G = p->ga_;
+  const size_t n = (size_t)p->n;
+  const int K = G.seg_cap;
+  cudaError_t e = cudaSuccess;
+  for (int j = L - 1; j >= 0 && e == cudaSuccess; --j) {
+    const CallArgs* ca = (first && j == L - 1) ? G.ca + 2 * K : G.ca + K + j;
+    e = launch_col(COL_ADMM_REV, kp_admm(p, ca, G.Wr, nullptr), s);
+    if (e == cudaSuccess) e = launch_mid(MID_ADMM_REV, kp_admm(p, G.ca + K + j, G.Wr, G.wseg + j * n), s);
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" cs_status cs_grad_admm(cs_plan_t p, const float* y, float lambda, const cs_admm_params* prm, int T, int K,
+                                  const float* gz_T, const float* gx_T, float* dc, float* dlambda, float* dy) {
+  if (!p || !y || !prm || !valid_ptr(gz_T) || (gx_T && !valid_ptr(gx_T)) || !valid_ptr(dc) || !dlambda || !dy ||
+      T < 1 || K < 1 || K > T || !(lambda >= 0.f) || !std::isfinite(lambda) || !(prm->sigma > 0.0) ||
+      !(prm->rho > 0.0) || !std::isfinite(prm->sigma) || !std::isfinite(prm->rho) || !std::isfinite(prm->tau1) ||
+      !std::isfinite(prm->tau2))
+    return CS_ERR_ARG;
+  if (p->ga.twod) return CS_ERR_UNSUPPORTED;
+  cudaStream_t s = p->stream;
+  const int S = (T + K - 1) / K;   // segments; segment sg covers iterations [sg K, min((sg+1) K, T))
+  CS_TRY(grad_admm_reserve(p, S, K));
+  auto& G = p->ga_;
+  const int Kc = G.seg_cap;
+  const size_t n = (size_t)p->n, nb = n * sizeof(float);
+  p->launches = 0;
+  if (prm->rho != p->b_rho || prm->sigma != p->b_sigma) {
+    CS_TRY(launch_tab_admm_b(p->abs2, (int)tab_count(p->ga), p->n, prm->rho, prm->sigma, p->tab_admm_b, s));
+    p->launches += 1;
+    p->b_rho = prm->rho;
+    p->b_sigma = prm->sigma;
+  }
+  CallArgs a{};
+  a.x = p->ax;
+  a.z = p->az;
+  a.mu = p->amu;
+  a.nu = p->anu;
+  a.v = p->av;
+  a.thr = (float)((double)lambda / prm->sigma);
+  a.rho = (float)prm->rho;
+  a.sigma = (float)prm->sigma;
+  a.tau1 = (float)prm->tau1;
+  a.tau2 = (float)prm->tau2;
+  a.d_on = (float)(1.0 / (1.0 + prm->rho));
+  a.d_off = (float)(1.0 / prm->rho);
+  CS_TRY(launch_set_args(a, p->ca, s));
+  CS_TRY(launch_scatter_y(y, p->sa.pos, p->m, p->sa.ys, p->status, s));
+  p->launches += 2;
+  p->ista_args = false;
+  p->admm_args = false;
+
+  // forward: T iterations of Algorithm 3 from the zero state, the state
+  // entering iteration sK kept
+  float* state[4] = {p->av, p->az, p->amu, p->anu};
+  for (float* b : state) CS_TRY(cudaMemsetAsync(b, 0, nb, s));
+  CS_TRY(launch_col(COL_ADMM_INIT, kparams(p, p->ga, 0), s));
+  p->launches += 1;
+  for (int sg = 0; sg < S; ++sg) {
+    const int L = (sg + 1) * K <= T ? K : T - sg * K;
+    for (int i = 0; i < 4; ++i)
+      CS_TRY(cudaMemcpyAsync(G.ckpt + (sg * 4 + i) * n, state[i], nb, cudaMemcpyDeviceToDevice, s));
+    CS_TRY(run_chunk(p, K_ADMM, L, sg == S - 1));
+  }
+
+  // per-iteration arguments: replay (state in the plan's buffers), reverse,
+  // the reverse of iteration T-1 (with dL/dz(T), dL/dx(T)), the output pass
+  for (int j = 0; j < Kc; ++j) {
+    CallArgs r = a;
+    r.x = nullptr;
+    r.aux = G.sseg + j * n;
+    CS_TRY(launch_set_args(r, G.ca + j, s));
+    CallArgs b = a;
+    b.x = nullptr;
+    b.z = nullptr;
+    b.mu = G.mub;
+    b.nu = G.nub;
+    b.v = G.dy;
+    b.aux = G.sseg + j * n;
+    CS_TRY(launch_set_args(b, G.ca + Kc + j, s));
+  }
+  {
+    CallArgs b = a;
+    b.x = nullptr;
+    b.z = nullptr;
+    b.mu = G.mub;
+    b.nu = G.nub;
+    b.v = G.dy;
+    const int jl = (T - (S - 1) * K) - 1;   // last iteration of the last segment
+    b.aux = G.sseg + jl * n;
+    b.src = G.gz;
+    b.xtrue = gx_T ? G.gx : nullptr;
+    CS_TRY(launch_set_args(b, G.ca + 2 * Kc, s));
+    CallArgs o{};
+    o.dst = dc;
+    CS_TRY(launch_set_args(o, G.ca + 2 * Kc + 1, s));
+  }
+  p->launches += 2 * Kc + 2;
+  CS_TRY(launch_to_tile(gz_T, G.gz, p->ga, 0, s));
+  if (gx_T) CS_TRY(launch_to_tile(gx_T, G.gx, p->ga, 0, s));
+  CS_TRY(cudaMemsetAsync(G.mub, 0, nb, s));
+  CS_TRY(cudaMemsetAsync(G.nub, 0, nb, s));
+  CS_TRY(cudaMemsetAsync(G.Wr, 0, n * sizeof(float2), s));
+  CS_TRY(cudaMemsetAsync(G.gacc, 0, tab_count(p->ga) * sizeof(float2), s));
+  CS_TRY(cudaMemsetAsync(G.gpart, 0, p->ga.col_ctas * sizeof(double), s));
+  CS_TRY(cudaMemsetAsync(G.dy, 0, p->m * sizeof(float), s));
+  p->launches += gx_T ? 2 : 1;
+
+  // reverse, segment by segment: replay from the checkpoint, then back-propagate
+  for (int sg = S - 1; sg >= 0; --sg) {
+    const int L = (sg + 1) * K <= T ? K : T - sg * K;
+    for (int i = 0; i < 4; ++i)
+      CS_TRY(cudaMemcpyAsync(state[i], G.ckpt + (sg * 4 + i) * n, nb, cudaMemcpyDeviceToDevice, s));
+    CS_TRY(run_graph(p, (uint64_t(5) << 40) | (uint32_t)L,
+                     [&](cudaStream_t st) { return enqueue_admm_replay(p, L, st); }));
+    const bool first = sg == S - 1;
+    CS_TRY(run_graph(p, (uint64_t(6) << 40) | ((uint64_t)first << 32) | (uint32_t)L,
+                     [&](cudaStream_t st) { return enqueue_admm_reverse(p, L, first, st); }));
+    p->launches += 1 + 2 * L + 2 * L;
+  }
+
+  // outputs: dL/dc from its spectrum, dL/dlambda = sum / sigma, dL/dy by row
+  CS_TRY(launch_mid(MID_ADMM_FROM_ACC, kp_admm(p, G.ca + 2 * Kc + 1, G.Wr, nullptr), s));
+  CS_TRY(launch_col(COL_STORE_RE, kp_admm(p, G.ca + 2 * Kc + 1, G.Wr, nullptr), s));
+  CS_TRY(launch_sum_scaled(G.gpart, p->ga.col_ctas, (float)(1.0 / prm->sigma), dlambda, s));
+  CS_TRY(launch_gather_rows(G.dy, p->sa.pos, p->m, dy, s));
+  p->launches += 4;
+  return CS_OK;
+}

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(ColTile<SHAPE>::kTile / EPT, ColTile<SHAPE>::k
     }
     __syncthreads();
   }
-  if constexpr (KIND == COL_GRAD_W) block_accum<NT>(acc.v[0], kp.pp.gpart);
+  if constexpr (KIND == COL_GRAD_W || KIND == COL_ADMM_REV) block_accum<NT>(acc.v[0], kp.pp.gpart);
   if (kp.flags & FL_STATS) {
     constexpr int kSlots =
         KIND == COL_RESIDUAL ? (1 << ST_R2)
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(ColTile<SHAPE>::kTile / EPT, ColTile<SHAPE>::k
   X(COL_LOAD, S) X(COL_LOAD_SCALED, S) X(COL_STORE, S) X(COL_MASK, S) X(COL_RESIDUAL, S)         \
   X(COL_ISTA, S) X(COL_ISTA_LAST, S) X(COL_POWER_OUT, S) X(COL_ADMM_INIT, S) X(COL_ADMM, S)       \
   X(COL_ADMM_LAST, S) X(COL_LOADT, S) X(COL_RES_SAVE, S) X(COL_ISTA_SEG, S) X(COL_GRAD_W, S)           \
-  X(COL_GRAD_MASK, S) X(COL_GRAD_G, S) X(COL_LOAD2, S)
+  X(COL_GRAD_MASK, S) X(COL_GRAD_G, S) X(COL_LOAD2, S) X(COL_ADMM_SEG, S) X(COL_ADMM_REV, S) X(COL_STORE_RE, S)
 
 cudaError_t init_col_kernels() {
   cudaError_t e = cudaSuccess;

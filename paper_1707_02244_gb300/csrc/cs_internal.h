@@ -57,6 +57,8 @@ struct PlanPtrs {
   float2* W2;                // second exchange buffer, complex[N] of the real-FFT geometry
   float4* gacc;              // per pair slot: accumulated spectrum at (k, k + N)
   double* gpart;             // per column CTA: accumulated dL/dtheta
+  // unrolled-ADMM gradient (cs_grad_admm) only
+  float2* gacc_a;            // per pair slot of the complex-n geometry: accumulated spectrum of dL/dc at k
 };
 
 // Per-call arguments, resident in device memory and written by a one-thread
@@ -106,12 +108,20 @@ enum ColKind : int {
   COL_GRAD_W,          // w = dst on the support of z -> mu, dtheta partials, forward
   COL_GRAD_MASK,       // inverse, q = M C w -> nu, aux += tau P C w, forward
   COL_GRAD_G,          // inverse, dst = mu - tau C^T q
-  COL_LOAD2            // forward FFTs of (v, mu) -> (W, W2); with FL_PAIR2 of (nu, x)
+  COL_LOAD2,           // forward FFTs of (v, mu) -> (W, W2); with FL_PAIR2 of (nu, x)
+  // unrolled-ADMM gradient (complex-n geometry, vectors in tile order)
+  COL_ADMM_SEG,        // as COL_ADMM (no state written), and s = x + nu -> aux
+  COL_ADMM_REV,        // inverse (b' + i C b'), reverse of one Algorithm 3 iteration, forward FFT of (p' + i x')
+  COL_STORE_RE         // inverse FFT, real part -> dst
 };
 enum MidKind : int {
   MID_FWD = 0, MID_ADJ, MID_ADMM,
   MID_CORR,            // forward FFTs of W and W2 -> gacc += s conj(a^) b^ (s = -1 with FL_PAIR2)
-  MID_FROM_ACC         // tau / N times the packed spectrum of gacc -> inverse FFT -> W
+  MID_FROM_ACC,        // tau / N times the packed spectrum of gacc -> inverse FFT -> W
+  // unrolled-ADMM gradient (complex-n geometry)
+  MID_ADMM_REV,        // FFTs of W (p' + i x') and W2 (the forward pair): b' = B (C^T p' + x'), dL/dc spectrum
+                       // -> gacc_a, inverse FFT of b' + i C b' -> W
+  MID_ADMM_FROM_ACC    // the Hermitian spectrum of gacc_a -> inverse FFT -> W
 };
 
 // Launchers (cs_passes.cu).  Return cudaGetLastError() of the launch.

@@ -344,6 +344,61 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
       kp.pp.gacc[tidx] = acc;
     }
     return;
+  } else if constexpr (KIND == MID_ADMM_REV) {
+    // Reverse of the x-update of one Algorithm 3 iteration.  W holds the
+    // column transform of p' + i x', W2 that of the iteration's forward pair
+    // v + i (z - nu).  Per pair slot, with the k-side spectra P', X'l, V0, Wf
+    // of the four real vectors: Xs = bhat (rho chat V0 + sigma Wf) and
+    // Bs = bhat (chat P' + X'l) are the spectra of x and b' = B (C^T p' + x')
+    // divided by N (bhat holds 1/N).  The spectrum of this iteration's dL/dc
+    // divided by N,
+    //   A = conj(P') Xs + rho conj(V0) Bs - 2 rho N chat Re(conj(Xs) Bs),
+    // is added to gacc_a (DFT of sum_i a_i b_{i+k} = conj(a^) b^; the B-term
+    // pairs C x with b' and C b' with x, whose sum is real times chat), and
+    // Bs + i conj(chat) Bs goes back for the inverse: b' + i C b'.
+    float2* sm2 = sm + smem_slots(TILE);
+    load_tile(sm, W);
+    fwd_rows(sm);
+    load_tile(sm2, kp.pp.W2);
+    fwd_rows(sm2);
+    const float rho = kp.ca->rho, sigma = kp.ca->sigma;
+    const float nN = (float)g.N;
+    for (int t = threadIdx.x; t < nslots; t += NT) {
+      int ea, eb, k2, k1, tidx;
+      slot_at(t, ea, eb, k2, k1, tidx);
+      const float2 za = sm[pad(ea)], zb = sm[pad(eb)];
+      const float2 fa = sm2[pad(ea)], fb = sm2[pad(eb)];
+      const float2 Pb = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+      const float2 Xl = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+      const float2 V0 = make_float2(0.5f * (fa.x + fb.x), 0.5f * (fa.y - fb.y));
+      const float2 Wf = make_float2(0.5f * (fa.y + fb.y), -0.5f * (fa.x - fb.x));
+      const float2 ch = __ldg(kp.pp.tab_admm_c + tidx);
+      const float bb = __ldg(kp.pp.tab_admm_b + tidx);
+      const float2 cv = cmul(ch, V0);
+      const float2 Xs = make_float2(bb * fmaf(rho, cv.x, sigma * Wf.x), bb * fmaf(rho, cv.y, sigma * Wf.y));
+      const float2 cp = cmul(ch, Pb);
+      const float2 Bs = make_float2(bb * (cp.x + Xl.x), bb * (cp.y + Xl.y));
+      const float2 t1 = cmulc(Xs, Pb);
+      const float2 t2 = cmulc(Bs, V0);
+      const float sc = -2.f * rho * nN * fmaf(Xs.x, Bs.x, Xs.y * Bs.y);
+      const float2 acc = kp.pp.gacc_a[tidx];
+      kp.pp.gacc_a[tidx] = make_float2(acc.x + fmaf(rho, t2.x, fmaf(sc, ch.x, t1.x)),
+                                       acc.y + fmaf(rho, t2.y, fmaf(sc, ch.y, t1.y)));
+      const float2 Pc = cmulc(Bs, ch);
+      sm[pad(eb)] = make_float2(Bs.x + Pc.y, Pc.x - Bs.y);   // self-pairs keep the k-side value
+      sm[pad(ea)] = make_float2(Bs.x - Pc.y, Bs.y + Pc.x);
+    }
+    __syncthreads();
+  } else if constexpr (KIND == MID_ADMM_FROM_ACC) {
+    // dL/dc = the inverse transform of the accumulated Hermitian spectrum
+    for (int t = threadIdx.x; t < nslots; t += NT) {
+      int ea, eb, k2, k1, tidx;
+      slot_at(t, ea, eb, k2, k1, tidx);
+      const float2 A = kp.pp.gacc_a[tidx];
+      sm[pad(eb)] = cconj(A);
+      sm[pad(ea)] = A;
+    }
+    __syncthreads();
   } else if constexpr (KIND == MID_FROM_ACC) {
     // The packed spectrum of the real vector d whose length-2N spectrum is
     // gacc (D_k, D_{k+N} per slot), times tau / N for the unnormalised
@@ -423,12 +478,13 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
 
 }  // namespace
 
-#define CS_MID_KINDS(X, T, S) \
-  X(MID_FWD, T, S) X(MID_ADJ, T, S) X(MID_ADMM, T, S) X(MID_CORR, T, S) X(MID_FROM_ACC, T, S)
+#define CS_MID_KINDS(X, T, S)                                                                    \
+  X(MID_FWD, T, S) X(MID_ADJ, T, S) X(MID_ADMM, T, S) X(MID_CORR, T, S) X(MID_FROM_ACC, T, S)       \
+  X(MID_ADMM_REV, T, S) X(MID_ADMM_FROM_ACC, T, S)
 #define CS_MID_KINDS_2D(X, T, S) X(MID_FWD, T, S) X(MID_ADJ, T, S) X(MID_ADMM, T, S)
 
-// MID_CORR holds two tiles in shared memory
-constexpr int mid_smem_mult(int kind) { return kind == MID_CORR ? 2 : 1; }
+// MID_CORR and MID_ADMM_REV hold two tiles in shared memory
+constexpr int mid_smem_mult(int kind) { return (kind == MID_CORR || kind == MID_ADMM_REV) ? 2 : 1; }
 
 cudaError_t init_mid_kernels() {
   cudaError_t e = cudaSuccess;

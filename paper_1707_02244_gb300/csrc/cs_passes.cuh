@@ -30,6 +30,8 @@ namespace csk {
 
 namespace {
 
+__device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
+
 __device__ __forceinline__ float soft(float u, float g) {
   // Eq. 4: sgn(u)(|u| - g) for |u| > g, else 0
   return u > g ? u - g : (u < -g ? u + g : 0.f);
@@ -98,7 +100,8 @@ struct RowSel {
 template <int KIND> struct UsesMask {
   static constexpr int kBits = (KIND == COL_RESIDUAL || KIND == COL_MASK || KIND == COL_RES_SAVE ||
                                 KIND == COL_GRAD_MASK) ? 2
-                              : (KIND == COL_ADMM || KIND == COL_ADMM_LAST) ? 1 : 0;
+                              : (KIND == COL_ADMM || KIND == COL_ADMM_LAST || KIND == COL_ADMM_SEG ||
+                                 KIND == COL_ADMM_REV) ? 1 : 0;
 };
 
 // Block sum of one per-thread value, added to dst[blockIdx.x] (one slot per
@@ -239,7 +242,7 @@ template <> struct Epi<COL_ADMM_INIT> {
 // Algorithm 3, after the x-update: v = D(rho C x - rho mu + P^T y),
 // z = eta_{lambda/sigma}(x + nu), mu += tau1 (v - C x), nu += tau2 (x - z),
 // v <- v + mu; the next x-update reads (v) + i (z - nu).
-template <bool FWD> struct EpiAdmm {
+template <bool FWD, bool SEG = false> struct EpiAdmm {
   static constexpr bool kRead = true, kFwd = FWD;
   __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2 xc, int p, int t, Acc& acc) {
     RowSel rs{acc.smask, acc.spref, acc.wbase};
@@ -252,6 +255,7 @@ template <bool FWD> struct EpiAdmm {
     const float d = on ? a.d_on : a.d_off;
     const float v = d * fmaf(a.rho, cx - mu, yv);
     const float z = soft(x + nu, a.thr);
+    if constexpr (SEG) a.aux[t] = x + nu;   // the soft threshold's input, for the reverse pass
     const float mu2 = fmaf(a.tau1, v - cx, mu);
     const float nu2 = fmaf(a.tau2, x - z, nu);
     const float vf = v + mu2;
@@ -280,6 +284,62 @@ template <bool FWD> struct EpiAdmm {
 };
 template <> struct Epi<COL_ADMM> : EpiAdmm<true> {};
 template <> struct Epi<COL_ADMM_LAST> : EpiAdmm<false> {};
+template <> struct Epi<COL_ADMM_SEG> : EpiAdmm<true, true> {};
+
+template <> struct Epi<COL_STORE_RE> {
+  static constexpr bool kRead = true, kFwd = false;
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2 v, int p, int t, Acc&) {
+    a.dst[p] = v.x;
+    return v;
+  }
+};
+
+// ------------------------------------------------ unrolled-ADMM gradient
+// Reverse mode of one Algorithm 3 iteration (state (v, z, mu, nu) -> (v2,
+// z1, mu1, nu1), see the forward epilogue above).  The inverse FFT brings
+// b' = B x' and C b' of the later iteration, which give the adjoints of the
+// new state: v2' = rho C b', z1' = sigma b' (+ dL/dz(T) at the last
+// iteration), mu1' (kept in mu) and nu1' = (kept in nu) - sigma b'.  Then
+//   mu1' += v2',  v1' = v2' + tau1 mu1',  p' = -tau1 mu1',  x' = tau2 nu1',
+//   z1' -= tau2 nu1',  s' = z1' on {|s| > lam/sigma},  x' += s',  nu' = nu1' + s',
+//   a' = D v1',  p' += rho a',  mu' = mu1' - rho a',  y' += P a',
+// with dL/dlam += -sum sign(s) s' / sigma (per-CTA partials; the host applies
+// 1/sigma).  mu' and nu' (without its -sigma b' term, added by the earlier
+// iteration's pass) go back to mu and nu; p' + i x' is transformed for the
+// mid pass, which forms x' + C^T p' and b' = B(...) there.  CallArgs: mu, nu
+// the adjoint state, aux = s of this iteration, v = dL/dy (compact rows, tile
+// order), src = dL/dz(T) and xtrue = dL/dx(T) at the last iteration only.
+template <> struct Epi<COL_ADMM_REV> {
+  static constexpr bool kRead = true, kFwd = true;
+  __device__ static float2 apply(const KParams&, const CallArgs& a, float2 bc, int p, int t, Acc& acc) {
+    RowSel rs{acc.smask, acc.spref, acc.wbase};
+    int iy;
+    const bool on = rs.get(t, iy);
+    const float b = bc.x, cb = bc.y;
+    const float vb = a.rho * cb;
+    float zb = a.sigma * b;
+    if (a.src) zb += __ldg(a.src + t);
+    float mub = a.mu[t] + vb;
+    float nub = fmaf(-a.sigma, b, a.nu[t]);
+    const float v1b = fmaf(a.tau1, mub, vb);
+    float pb = -a.tau1 * mub;
+    float xb = a.tau2 * nub;
+    if (a.xtrue) xb += __ldg(a.xtrue + t);
+    zb = fmaf(-a.tau2, nub, zb);
+    const float sv = __ldg(a.aux + t);
+    const float sb = fabsf(sv) > a.thr ? zb : 0.f;
+    acc.v[0] -= sgnf(sv) * sb;
+    xb += sb;
+    nub += sb;
+    const float ab = (on ? a.d_on : a.d_off) * v1b;
+    pb = fmaf(a.rho, ab, pb);
+    mub = fmaf(-a.rho, ab, mub);
+    if (on) a.v[iy] += ab;   // each compact row belongs to one element: plain read-modify-write
+    a.mu[t] = mub;
+    a.nu[t] = nub;
+    return make_float2(pb, xb);
+  }
+};
 
 // ------------------------------------------------ unrolled-ISTA gradient
 // Reverse mode of T steps x(t+1) = eta_theta(u(t)), u(t) = x(t) + tau C^T r(t),
@@ -323,7 +383,6 @@ template <> struct Epi<COL_ISTA_SEG> {
   }
 };
 
-__device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
 
 template <> struct Epi<COL_GRAD_W> {
   static constexpr bool kRead = false, kFwd = true;

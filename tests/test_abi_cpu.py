@@ -79,6 +79,10 @@ def test_null_plan_is_an_argument_error(cs):
     L = ctypes.c_double()
     assert cs.raw_call("cs_opnorm2", None, 10, ctypes.byref(L)) == cs.CS_ERR_ARG
     assert cs.raw_call("cs_set_monitor", None, None, ctypes.c_double(0.0), 10) == cs.CS_ERR_ARG
+    prm = cs.CsAdmmParams(1.0, 1.0, 1.0, 1.0)
+    buf = ctypes.c_void_p(8)
+    assert cs.raw_call("cs_grad_admm", None, buf, ctypes.c_float(0.1), ctypes.byref(prm), 10, 5, buf, None, buf,
+                       buf, buf) == cs.CS_ERR_ARG
 
 
 def test_batch_plan_rejects_bad_arguments_without_device(cs):

@@ -637,7 +637,9 @@ def run_grad(args):
     n/100, noise 1e-3, lambda = 5e-3, tau = 0.9/||C||^2 by power iteration),
     loss ||x(T) - x*||^2; one step = cs_grad (forward with checkpoints every
     25 steps, replay, reverse) against the plain solve cs_ista(T) on the same
-    plan.  Device-timed, L2 flushed between steps."""
+    plan.  The same for unrolled ADMM (T = 300, sigma = rho = 1, loss
+    ||z(T) - x*||^2): cs_grad_admm against cs_admm(T).  Device-timed, L2
+    flushed between steps."""
     import torch
     import paper_1707_02244_gb300 as cs
 
@@ -668,6 +670,18 @@ def run_grad(args):
     def grad():
         cs.cs_grad(plan, y, LAM, tau, T, K, gx, dc, dl, dy)
 
+    # unrolled ADMM (Algorithm 3, sigma = rho = 1) on the same instance, loss
+    # ||z(T) - x*||^2
+    z = torch.zeros(n, dtype=torch.float32, device=dev)
+    cs.cs_admm(plan, y, LAM, RHO, T, z, stats=False)
+    gz = 2.0 * (z - xt)
+
+    def solve_admm():
+        cs.cs_admm(plan, y, LAM, RHO, T, z, stats=False)
+
+    def grad_admm():
+        cs.cs_grad_admm(plan, y, LAM, RHO, RHO, 1.0, 1.0, T, K, gz, dc, dl, dy)
+
     def timed(fn):
         for _ in range(args.warmup):
             fn()
@@ -687,6 +701,8 @@ def run_grad(args):
     clocks.start()
     ms_g = timed(grad)
     ms_s = timed(solve)
+    ms_ga = timed(grad_admm)
+    ms_sa = timed(solve_admm)
     clk = clocks.stop()
     assert cs.cs_status_sync(plan) == cs.CS_OK
     line = {
@@ -698,6 +714,8 @@ def run_grad(args):
                    "l2": "flushed (512 MiB write) between steps, outside the timed events"},
         "plain_solve_ms": ms_s, "grad_over_solve": ms_g / ms_s,
         "grad_ms_per_unrolled_step": ms_g / T, "solve_ms_per_iter": ms_s / T,
+        "admm": {"grad_ms": ms_ga, "plain_solve_ms": ms_sa, "grad_over_solve": ms_ga / ms_sa,
+                 "loss": "||z_T - x*||^2, sigma = rho = 1, tau1 = tau2 = 1, checkpoints every 25"},
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

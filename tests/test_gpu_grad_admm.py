@@ -74,6 +74,8 @@ def test_admm_grad_matches_oracle(cs, n, m, k, T, K, prm, with_x):
     inst, y32, lam = _setup(n, m, k, 9000 + n + T)
     gz, gx, o = _oracle(inst, y32, lam, prm, T, with_x)
     dc, dl, dy = _gpu_grad(cs, inst, y32, lam, prm, T, K, gz, gx)
+    print(f"n={n} T={T} K={K}: rel l2 dc {rel_l2(dc, o['dc']):.2e}, dy {rel_l2(dy, o['dy']):.2e}, "
+          f"dlam {abs(dl - o['dlam']) / max(abs(o['dlam']), 1e-12):.2e}")
     assert rel_l2(dc, o["dc"]) <= GRAD_TOL, ("dc", rel_l2(dc, o["dc"]))
     assert rel_l2(dy, o["dy"]) <= GRAD_TOL, ("dy", rel_l2(dy, o["dy"]))
     assert abs(dl - o["dlam"]) <= GRAD_TOL * max(abs(o["dlam"]), 1e-12), ("dlam", dl, o["dlam"])

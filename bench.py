@@ -490,9 +490,6 @@ def run_batched(args):
     """Batched solves against looping the plain solver (see the module
     docstring); 1 GPU, device-timed with CUDA events, L2 flushed between
     steps."""
-    # the batch's side streams need their own hardware queues (set before
-    # the CUDA context exists)
-    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
     import paper_1707_02244_gb300 as cs
 

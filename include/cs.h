@@ -219,19 +219,17 @@ cs_status cs_grad_admm(cs_plan_t plan, const float* y, float lambda, const cs_ad
  * for many independent instances at once).  Instance i has its own n_i,
  * m_i, rows and c.  Instances with n_i <= CS_BATCH_MAX_N are solved one CTA
  * per instance, the iterate kept in shared memory for all iterations (one
- * launch per power-of-two size class); larger instances by a per-instance
- * plan.  The work runs on internal streams (32; the environment variable
- * CS_BATCH_STREAMS, read by cs_batch_plan, sets 1..32) that fork from and
- * join back into the batch's stream, so instances overlap on the GPU.  They
- * only run side by side if the process has as many hardware queues: set
- * CUDA_DEVICE_MAX_CONNECTIONS=32 before the CUDA context is created (the
- * CUDA default, 8, serialises the streams beyond the eighth).
+ * launch per power-of-two size class, on up to 4 internal streams forked
+ * from the batch's stream).  Larger instances each have the buffers and
+ * tables of a plan, but are iterated together: every pass of an iteration
+ * is one launch over the tiles of all of them, so their whole solve is one
+ * CUDA graph launch on the batch's stream.
  * --------------------------------------------------------------------- */
 #define CS_BATCH_MAX_N 8192
 typedef struct cs_batch_s* cs_batch_t;
 
 /*   count     number of instances (>= 1)
- *   n, m      HOST int64[count]: n_i power of two, 64 <= n_i <= 2^22;
+ *   n, m      HOST int64[count]: n_i power of two, 64 <= n_i <= 2^21;
  *             1 <= m_i <= n_i
  *   rows      HOST int64[sum m_i]: instance i's rows, concatenated
  *   c         HOST float64[sum n_i]: instance i's first row of C, concatenated

@@ -1194,3 +1194,39 @@ extern "C" cs_status cs_grad_admm(cs_plan_t p, const float* y, float lambda, con
   p->launches += 4;
   return CS_OK;
 }
+
+// ------------------------------------------------------ grouped launches
+
+namespace csk {
+
+PlanView plan_view(cs_plan_s* p) {
+  PlanView v{};
+  v.kp_i = kparams(p, p->gi, 0);
+  v.kp_a = kparams(p, p->ga, 0);
+  GroupDesc& d = v.desc;
+  d.gi = p->gi;
+  d.ga = p->ga;
+  d.m = p->m;
+  d.pos_i = p->si.pos;
+  d.ys_i = p->si.ys;
+  d.pos_a = p->sa.pos;
+  d.ys_a = p->sa.ys;
+  d.xi_t = p->xi_t;
+  d.av = p->av;
+  d.az = p->az;
+  d.amu = p->amu;
+  d.anu = p->anu;
+  return v;
+}
+
+cudaError_t plan_admm_table(cs_plan_s* p, double rho, double sigma, cudaStream_t s) {
+  if (rho == p->b_rho && sigma == p->b_sigma) return cudaSuccess;
+  cudaError_t e = launch_tab_admm_b(p->abs2, (int)tab_count(p->ga), p->n, rho, sigma, p->tab_admm_b, s);
+  if (e == cudaSuccess) {
+    p->b_rho = rho;
+    p->b_sigma = sigma;
+  }
+  return e;
+}
+
+}  // namespace csk

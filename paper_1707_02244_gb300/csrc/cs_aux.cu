@@ -1,5 +1,6 @@
 // Plan-time and bookkeeping kernels: FP64 spectrum of c, twiddle and spectrum
 // tables, the row mask of Omega, y scatter / gather, deterministic reductions.
+#include "cs_fft.cuh"
 #include "cs_internal.h"
 
 namespace csk {
@@ -38,17 +39,18 @@ __global__ void twiddle_k(float2* dst, int count, int64_t M) {
   dst[q] = make_float2((float)c, (float)s);
 }
 
-// Stage-major twiddle table of a length-L FFT (see stockham_stage): stage
-// with span Ls and radix R holds w_{Ls R}^(r k) at (r - 1) Ls + k.
+// Stage-major twiddle table of a length-L FFT (see stage_twiddle): the
+// stage with span Ls and radix R holds w_{Ls R}^(r k) at row(r) Ls + k for
+// the rows r it keeps (tw_row_r).
 __global__ void stage_tw_k(float2* dst, int lgL, int count) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
   int lgLs = 4;
   while (true) {
     const int lgR = (lgL - lgLs) >= 4 ? 4 : (lgL - lgLs);
-    const int sz = ((1 << lgR) - 1) << lgLs;
+    const int sz = tw_rows(lgR) << lgLs;
     if (t < sz) {
-      const int r = (t >> lgLs) + 1, k = t & ((1 << lgLs) - 1);
+      const int r = tw_row_r(lgR, t >> lgLs), k = t & ((1 << lgLs) - 1);
       double sn, cs;
       sincospi(-2.0 * (double)(r * k) / (double)(1 << (lgLs + lgR)), &sn, &cs);
       dst[blockIdx.x * blockDim.x + threadIdx.x] = make_float2((float)cs, (float)sn);
@@ -470,6 +472,80 @@ cudaError_t launch_from_tile(const void* tiled, void* nat, const Geo& g, int com
     from_tile_k<float2><<<blocks_for(g.N), AUX_NT, 0, s>>>((const float2*)tiled, (float2*)nat, g);
   else
     from_tile_k<float><<<blocks_for(g.N), AUX_NT, 0, s>>>((const float*)tiled, (float*)nat, g);
+  return cudaGetLastError();
+}
+
+// ---- grouped element-wise kernels (blockIdx.y: the plan, grid-stride in x)
+
+__global__ void group_scatter_y_k(const GroupDesc* __restrict__ d, const float* __restrict__ y, int geo,
+                                  int* status) {
+  const GroupDesc& g = d[blockIdx.y];
+  const int32_t* pos = geo ? g.pos_a : g.pos_i;
+  float* ys = geo ? g.ys_a : g.ys_i;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < g.m; r += (int64_t)gridDim.x * blockDim.x) {
+    const float v = y[g.moff + r];
+    if (!isfinite(v)) atomicOr(status, STS_NONFINITE);
+    ys[pos[r]] = v;
+  }
+}
+
+template <bool IN>
+__global__ void group_ista_k(const GroupDesc* __restrict__ d, float* x) {
+  const GroupDesc& g = d[blockIdx.y];
+  float2* xn = reinterpret_cast<float2*>(x + g.noff);
+  float2* xt = reinterpret_cast<float2*>(g.xi_t);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.gi.N; t += (int64_t)gridDim.x * blockDim.x) {
+    if (IN) xt[t] = xn[tile_to_nat(g.gi, t)];
+    else xn[tile_to_nat(g.gi, t)] = xt[t];
+  }
+}
+
+__global__ void group_admm_zero_k(const GroupDesc* __restrict__ d) {
+  const GroupDesc& g = d[blockIdx.y];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.ga.N; t += (int64_t)gridDim.x * blockDim.x) {
+    g.av[t] = 0.f;
+    g.az[t] = 0.f;
+    g.amu[t] = 0.f;
+    g.anu[t] = 0.f;
+  }
+}
+
+__global__ void group_admm_out_k(const GroupDesc* __restrict__ d, float* z) {
+  const GroupDesc& g = d[blockIdx.y];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.ga.N; t += (int64_t)gridDim.x * blockDim.x)
+    z[g.noff + tile_to_nat(g.ga, t)] = g.az[t];
+}
+
+constexpr unsigned GROUP_GX = 32;   // CTAs per plan in the grouped element-wise kernels
+
+cudaError_t launch_group_scatter_y(const GroupDesc* d, int count, const float* y, int geo, int* status,
+                                   cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  group_scatter_y_k<<<dim3(GROUP_GX, count), AUX_NT, 0, s>>>(d, y, geo, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_ista_in(const GroupDesc* d, int count, const float* x, cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  group_ista_k<true><<<dim3(GROUP_GX, count), AUX_NT, 0, s>>>(d, const_cast<float*>(x));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_ista_out(const GroupDesc* d, int count, float* x, cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  group_ista_k<false><<<dim3(GROUP_GX, count), AUX_NT, 0, s>>>(d, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_admm_zero(const GroupDesc* d, int count, cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  group_admm_zero_k<<<dim3(GROUP_GX, count), AUX_NT, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_admm_out(const GroupDesc* d, int count, float* z, cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  group_admm_out_k<<<dim3(GROUP_GX, count), AUX_NT, 0, s>>>(d, z);
   return cudaGetLastError();
 }
 

@@ -1,14 +1,19 @@
-// Batched solver: many independent instances A_i = P_i C(c_i) of uneven size
-// in one launch.  Every instance with n <= CS_BATCH_MAX_N is solved by one
-// CTA that keeps its iterate in shared memory for all iterations (no global
-// exchange at all: the whole FFT of the instance fits in the CTA); CTAs are
-// ordered largest instance first.  Larger instances of the batch are solved
-// by a per-instance plan of the multipass path.
+// Batched solver: many independent instances A_i = P_i C(c_i) of uneven size.
+// Every instance with n <= CS_BATCH_MAX_N is solved by one CTA that keeps its
+// iterate in shared memory for all iterations (no global exchange at all: the
+// whole FFT of the instance fits in the CTA); CTAs are ordered largest
+// instance first, one launch per power-of-two size class.  Larger instances
+// have their own plan's buffers and tables but are iterated together: each
+// pass of an iteration is one grouped launch over the tiles of all of them
+// (col_kernel_multi / mid_kernel_multi), so a whole solve of every large
+// instance is one captured CUDA graph on the batch's stream, ordered by the
+// kernel boundaries alone.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <map>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -23,7 +28,7 @@ namespace {
 constexpr int LG_TW = 13;       // master twiddle table exp(-2 pi i q / 8192)
 constexpr int BI_LG_MIN = 5, BI_LG_MAX = 12;   // ISTA: packed length N = n/2 = 2^LG
 constexpr int BA_LG_MIN = 6, BA_LG_MAX = 13;   // ADMM: complex length n = 2^LG
-constexpr int NSIDE_MAX = 32;   // side streams the instances are spread over (CS_BATCH_STREAMS, default 32)
+constexpr int NSIDE_MAX = 4;    // side streams of the size-class launches (within CUDA's default 8 queues)
 
 struct BatchDesc {
   int n, lgn, m;
@@ -336,7 +341,18 @@ struct cs_batch_s {
   std::vector<int> small;           // instances solved by the single-CTA kernels, largest first
   std::vector<int> large;           // instances solved by their own plan
   std::vector<cs_plan_t> plans;     // per large instance
-  std::vector<int> plan_side;       // side stream of each large instance's plan
+  // grouped launches over the large instances (in the order of `large`)
+  struct Group {
+    int count = 0;
+    std::vector<GroupDesc> hdesc;
+    GroupDesc* desc = nullptr;
+    KParams *kps_i = nullptr, *kps_a0 = nullptr, *kps_a1 = nullptr;
+    CallArgs* ca = nullptr;
+    int2 *map_col_i = nullptr, *map_mid_i = nullptr, *map_col_a = nullptr, *map_mid_a = nullptr;
+    int n_col_i = 0, n_mid_i = 0, n_col_a = 0, n_mid_a = 0;
+    cudaStream_t cap = nullptr;
+    std::map<uint64_t, cudaGraphExec_t> graphs;
+  } grp;
   struct Class {
     int lgn, start, count, side;    // instances order[start, start + count) have n = 2^lgn
   };
@@ -382,6 +398,12 @@ void batch_free(cs_batch_s* b) {
     if (b->side_done[k]) cudaEventDestroy(b->side_done[k]);
   }
   if (b->fork) cudaEventDestroy(b->fork);
+  auto& G = b->grp;
+  for (auto& kv : G.graphs) cudaGraphExecDestroy(kv.second);
+  void* gb[] = {G.desc, G.kps_i, G.kps_a0, G.kps_a1, G.ca, G.map_col_i, G.map_mid_i, G.map_col_a, G.map_mid_a};
+  for (void* q : gb)
+    if (q) cudaFree(q);
+  if (G.cap) cudaStreamDestroy(G.cap);
   delete b;
 }
 
@@ -419,6 +441,63 @@ cudaError_t join_sides(cs_batch_s* b) {
   return e;
 }
 
+// Run `enqueue` on the batch's stream as a cached CUDA graph under `key`.
+template <class F>
+cudaError_t run_group_graph(cs_batch_s* b, uint64_t key, F&& enqueue) {
+  auto& G = b->grp;
+  auto it = G.graphs.find(key);
+  if (it == G.graphs.end()) {
+    cudaError_t e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t e2 = enqueue(G.cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(G.cap, &graph);
+    if (e2 != cudaSuccess || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return e2 != cudaSuccess ? e2 : e;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    it = G.graphs.emplace(key, exec).first;
+  }
+  return cudaGraphLaunch(it->second, b->stream);
+}
+
+// T iterations of Algorithm 1 on every large instance: per iteration four
+// grouped passes (C x, residual, C^T r, update), each over the tiles of all
+// of them.
+cudaError_t enqueue_group_ista(cs_batch_s* b, int T, cudaStream_t s) {
+  auto& G = b->grp;
+  cudaError_t e = launch_col_multi(COL_LOAD, G.kps_i, G.map_col_i, G.n_col_i, s);
+  for (int t = 0; t < T && e == cudaSuccess; ++t) {
+    e = launch_mid_multi(MID_FWD, G.kps_i, G.map_mid_i, G.n_mid_i, s);
+    if (e == cudaSuccess) e = launch_col_multi(COL_RESIDUAL, G.kps_i, G.map_col_i, G.n_col_i, s);
+    if (e == cudaSuccess) e = launch_mid_multi(MID_ADJ, G.kps_i, G.map_mid_i, G.n_mid_i, s);
+    if (e == cudaSuccess)
+      e = launch_col_multi(t + 1 < T ? COL_ISTA : COL_ISTA_LAST, G.kps_i, G.map_col_i, G.n_col_i, s);
+  }
+  return e;
+}
+
+// T iterations of Algorithm 3 on every large instance: per iteration the
+// grouped x-update (mid pass) and elementwise steps (column pass); the last
+// one writes z.
+cudaError_t enqueue_group_admm(cs_batch_s* b, int T, cudaStream_t s) {
+  auto& G = b->grp;
+  cudaError_t e = launch_col_multi(COL_ADMM_INIT, G.kps_a0, G.map_col_a, G.n_col_a, s);
+  for (int t = 0; t < T && e == cudaSuccess; ++t) {
+    e = launch_mid_multi(MID_ADMM, G.kps_a0, G.map_mid_a, G.n_mid_a, s);
+    if (e == cudaSuccess) {
+      const bool last = t + 1 == T;
+      e = launch_col_multi(last ? COL_ADMM_LAST : COL_ADMM, last ? G.kps_a1 : G.kps_a0,
+                           G.map_col_a, G.n_col_a, s);
+    }
+  }
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -428,17 +507,14 @@ cs_status cs_batch_plan(cs_batch_t* out, int count, const int64_t* n, const int6
   if (!out || count < 1 || !n || !m || !rows || !c) return CS_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
-    if (n[i] < 64 || n[i] > (int64_t(1) << 22) || !pow2(n[i])) return CS_ERR_UNSUPPORTED;
+    if (n[i] < 64 || n[i] > (int64_t(1) << 21) || !pow2(n[i])) return CS_ERR_UNSUPPORTED;
     if (m[i] < 1 || m[i] > n[i]) return CS_ERR_ARG;
   }
   cs_batch_s* b = new (std::nothrow) cs_batch_s();
   if (!b) return CS_ERR_NOMEM;
   b->count = count;
   b->stream = static_cast<cudaStream_t>(stream);
-  if (const char* env = std::getenv("CS_BATCH_STREAMS")) {
-    const int v = std::atoi(env);
-    if (v >= 1) b->nside = std::min(v, NSIDE_MAX);
-  }
+
   cudaStream_t s = b->stream;
   b->n.assign(n, n + count);
   b->m.assign(m, m + count);
@@ -475,10 +551,11 @@ cs_status cs_batch_plan(cs_batch_t* out, int count, const int64_t* n, const int6
   b->atab_tot = at;
   std::stable_sort(b->small.begin(), b->small.end(), [&](int a, int c2) { return n[a] > n[c2]; });
   std::stable_sort(b->large.begin(), b->large.end(), [&](int a, int c2) { return n[a] > n[c2]; });
-  // Work items (one launch per size class of small instances, one plan per
-  // large instance) go to the side streams longest first, each to the
-  // stream with the least work so far (cost ~ n per iteration; a class runs
-  // its instances side by side, about 2 * 152 at a time).
+  // The size-class launches of the small instances go to the side streams
+  // longest first, each to the stream with the least work so far (cost ~ n
+  // per iteration; a class runs its instances side by side, about 2 * 152 at
+  // a time); the grouped launches of the large instances run on the batch's
+  // stream.
   for (size_t j = 0; j < b->small.size();) {
     const int lg = hd[b->small[j]].lgn;
     size_t e = j;
@@ -493,15 +570,12 @@ cs_status cs_batch_plan(cs_batch_t* out, int count, const int64_t* n, const int6
       const auto& cl = b->classes[j];
       items.push_back({(double)(int64_t(1) << cl.lgn) * (double)((cl.count + 303) / 304), 0, (int)j});
     }
-    for (size_t j = 0; j < b->large.size(); ++j) items.push_back({(double)n[b->large[j]], 1, (int)j});
     std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& c2) { return a.cost > c2.cost; });
     double load[NSIDE_MAX] = {};
-    b->plan_side.assign(b->large.size(), 0);
     for (const Item& itm : items) {
       const int k = (int)(std::min_element(load, load + b->nside) - load);
       load[k] += itm.cost;
-      if (itm.kind == 0) b->classes[itm.idx].side = k;
-      else b->plan_side[itm.idx] = k;
+      b->classes[itm.idx].side = k;
     }
   }
   auto fail = [&](cs_status e) {
@@ -518,13 +592,63 @@ cs_status cs_batch_plan(cs_batch_t* out, int count, const int64_t* n, const int6
     CS_B_TRY(cudaEventCreateWithFlags(&b->side_done[k], cudaEventDisableTiming));
   }
   CS_B_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
-  // large instances: their own plans, each on its side stream
+  // large instances: their own plans (buffers, tables, masks) on the batch's
+  // stream, and the parameters of the grouped launches over all of them
   for (size_t j = 0; j < b->large.size(); ++j) {
     const int i = b->large[j];
     cs_plan_t p = nullptr;
-    const cs_status st = cs_plan(&p, n[i], m[i], rows + b->moff[i], c + b->noff[i], b->side[b->plan_side[j]]);
+    const cs_status st = cs_plan(&p, n[i], m[i], rows + b->moff[i], c + b->noff[i], s);
     if (st != CS_OK) return fail(st);
     b->plans.push_back(p);
+  }
+  if (!b->large.empty()) {
+    auto& G = b->grp;
+    G.count = (int)b->large.size();
+    CS_B_TRY(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+    CS_B_TRY(balloc(&G.desc, G.count));
+    CS_B_TRY(balloc(&G.kps_i, G.count));
+    CS_B_TRY(balloc(&G.kps_a0, G.count));
+    CS_B_TRY(balloc(&G.kps_a1, G.count));
+    CS_B_TRY(balloc(&G.ca, G.count));
+    std::vector<KParams> ki(G.count), ka0(G.count), ka1(G.count);
+    std::vector<int2> mci, mmi, mca, mma;
+    for (int j = 0; j < G.count; ++j) {
+      const int i = b->large[j];
+      const PlanView v = plan_view(b->plans[j]);
+      GroupDesc d = v.desc;
+      d.noff = b->noff[i];
+      d.moff = b->moff[i];
+      G.hdesc.push_back(d);
+      ki[j] = v.kp_i;
+      ka0[j] = v.kp_a;
+      ki[j].ca = ka0[j].ca = G.ca + j;
+      ka1[j] = ka0[j];
+      ka1[j].flags = FL_WRITE_STATE;
+      for (int t = 0; t < d.gi.col_ctas; ++t) mci.push_back(make_int2(j, t));
+      for (int t = 0; t < d.gi.mid_ctas; ++t) mmi.push_back(make_int2(j, t));
+      for (int t = 0; t < d.ga.col_ctas; ++t) mca.push_back(make_int2(j, t));
+      for (int t = 0; t < d.ga.mid_ctas; ++t) mma.push_back(make_int2(j, t));
+      // grouped launches take 4096-value tiles and run-time shapes only
+      if (d.gi.tile != 4096 || d.ga.tile != 4096 || d.gi.col_tile != 4096 || d.ga.col_tile != 4096)
+        return fail(CS_ERR_UNSUPPORTED);
+    }
+    G.n_col_i = (int)mci.size();
+    G.n_mid_i = (int)mmi.size();
+    G.n_col_a = (int)mca.size();
+    G.n_mid_a = (int)mma.size();
+    CS_B_TRY(balloc(&G.map_col_i, mci.size()));
+    CS_B_TRY(balloc(&G.map_mid_i, mmi.size()));
+    CS_B_TRY(balloc(&G.map_col_a, mca.size()));
+    CS_B_TRY(balloc(&G.map_mid_a, mma.size()));
+    CS_B_TRY(cudaMemcpyAsync(G.desc, G.hdesc.data(), G.count * sizeof(GroupDesc), cudaMemcpyHostToDevice, s));
+    CS_B_TRY(cudaMemcpyAsync(G.kps_i, ki.data(), G.count * sizeof(KParams), cudaMemcpyHostToDevice, s));
+    CS_B_TRY(cudaMemcpyAsync(G.kps_a0, ka0.data(), G.count * sizeof(KParams), cudaMemcpyHostToDevice, s));
+    CS_B_TRY(cudaMemcpyAsync(G.kps_a1, ka1.data(), G.count * sizeof(KParams), cudaMemcpyHostToDevice, s));
+    CS_B_TRY(cudaMemcpyAsync(G.map_col_i, mci.data(), mci.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    CS_B_TRY(cudaMemcpyAsync(G.map_mid_i, mmi.data(), mmi.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    CS_B_TRY(cudaMemcpyAsync(G.map_col_a, mca.data(), mca.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    CS_B_TRY(cudaMemcpyAsync(G.map_mid_a, mma.data(), mma.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    CS_B_TRY(cudaStreamSynchronize(s));
   }
   if (!b->small.empty()) {
     for (int lg = BI_LG_MIN; lg <= BI_LG_MAX; ++lg) {
@@ -607,6 +731,11 @@ cs_status cs_batch_plan(cs_batch_t* out, int count, const int64_t* n, const int6
     b->host_rho.assign(count, -1.0);
     b->host_sigma.assign(count, -1.0);
   }
+  if (!b->status) {
+    CS_B_TRY(balloc(&b->status, 1));
+    CS_B_TRY(cudaMemsetAsync(b->status, 0, sizeof(int), s));
+  }
+  CS_B_TRY(cudaStreamSynchronize(s));
   for (int k = 0; k < b->nside; ++k) CS_B_TRY(cudaStreamSynchronize(b->side[k]));
 #undef CS_B_TRY
   *out = b;
@@ -640,9 +769,26 @@ cs_status cs_batch_ista(cs_batch_t b, const float* y, const float* lambda, const
     batch_scatter_k<<<nb256(b->mtot), 256, 0, s>>>(y, b->pos, b->mtot, b->ys, b->status);
   }
   cs_status st = cstat(fork_sides(b));
-  for (size_t j = 0; j < b->large.size() && st == CS_OK; ++j) {
-    const int i = b->large[j];
-    st = cs_ista(b->plans[j], y + b->moff[i], lambda[i], tau[i], iters, x + b->noff[i], nullptr);
+  if (!b->large.empty() && st == CS_OK) {
+    auto& G = b->grp;
+    std::vector<CallArgs> h(G.count);
+    for (int j = 0; j < G.count; ++j) {
+      const int i = b->large[j];
+      h[j] = CallArgs{};
+      h[j].src = x + b->noff[i];   // COL_LOAD transforms x(0) in natural order
+      h[j].x = G.hdesc[j].xi_t;    // the iterate lives in tile order during the solve
+      h[j].thr = (float)((double)tau[i] * (double)lambda[i]);
+      h[j].tau = tau[i];
+    }
+    st = cstat(cudaMemcpyAsync(G.ca, h.data(), G.count * sizeof(CallArgs), cudaMemcpyHostToDevice, s));
+    if (st == CS_OK) st = cstat(launch_group_scatter_y(G.desc, G.count, y, 0, b->status, s));
+    if (st == CS_OK && iters > 0) {
+      st = cstat(launch_group_ista_in(G.desc, G.count, x, s));
+      if (st == CS_OK)
+        st = cstat(run_group_graph(b, (uint64_t(1) << 40) | (uint32_t)iters,
+                                   [&](cudaStream_t cs) { return enqueue_group_ista(b, iters, cs); }));
+      if (st == CS_OK) st = cstat(launch_group_ista_out(G.desc, G.count, x, s));
+    }
   }
   if (iters > 0) {
     for (const auto& cl : b->classes) {
@@ -702,9 +848,34 @@ cs_status cs_batch_admm(cs_batch_t b, const float* y, const float* lambda, const
     batch_scatter_k<<<nb256(b->mtot), 256, 0, s>>>(y, b->pos, b->mtot, b->ys, b->status);
   }
   st = cstat(fork_sides(b));
-  for (size_t j = 0; j < b->large.size() && st == CS_OK; ++j) {
-    const int i = b->large[j];
-    st = cs_admm(b->plans[j], y + b->moff[i], lambda[i], rho[i], iters, z + b->noff[i], nullptr);
+  if (!b->large.empty() && st == CS_OK) {
+    // sigma = rho, tau1 = tau2 = 1 (as cs_admm), zero start
+    auto& G = b->grp;
+    std::vector<CallArgs> h(G.count);
+    for (int j = 0; j < G.count && st == CS_OK; ++j) {
+      const int i = b->large[j];
+      const double r = rho[i];
+      st = cstat(plan_admm_table(b->plans[j], r, r, s));
+      h[j] = CallArgs{};
+      h[j].z = G.hdesc[j].az;
+      h[j].mu = G.hdesc[j].amu;
+      h[j].nu = G.hdesc[j].anu;
+      h[j].v = G.hdesc[j].av;
+      h[j].thr = (float)((double)lambda[i] / r);
+      h[j].rho = (float)r;
+      h[j].sigma = (float)r;
+      h[j].tau1 = 1.f;
+      h[j].tau2 = 1.f;
+      h[j].d_on = (float)(1.0 / (1.0 + r));
+      h[j].d_off = (float)(1.0 / r);
+    }
+    if (st == CS_OK) st = cstat(cudaMemcpyAsync(G.ca, h.data(), G.count * sizeof(CallArgs), cudaMemcpyHostToDevice, s));
+    if (st == CS_OK) st = cstat(launch_group_admm_zero(G.desc, G.count, s));
+    if (st == CS_OK) st = cstat(launch_group_scatter_y(G.desc, G.count, y, 1, b->status, s));
+    if (st == CS_OK && iters > 0)
+      st = cstat(run_group_graph(b, (uint64_t(2) << 40) | (uint32_t)iters,
+                                 [&](cudaStream_t cs) { return enqueue_group_admm(b, iters, cs); }));
+    if (st == CS_OK) st = cstat(launch_group_admm_out(G.desc, G.count, z, s));
   }
   if (iters > 0) {
     for (const auto& cl : b->classes) {

@@ -83,8 +83,9 @@ template <int SHAPE> struct ColTile {
   static constexpr int kLgN2 = SHAPE == 3 ? 12 : 10;   // static shapes
 };
 
+// The column pass of tile `blk` (columns blk G .. blk G + G - 1).
 template <int KIND, int SHAPE>
-__global__ void __launch_bounds__(ColTile<SHAPE>::kTile / EPT, ColTile<SHAPE>::kMinB) col_kernel(const KParams kp) {
+__device__ __forceinline__ void col_body(const KParams& kp, const int blk) {
   constexpr int TILE = ColTile<SHAPE>::kTile;
   constexpr int NT = Cfg<TILE>::NT;
   constexpr int NLD = Cfg<TILE>::NLD;
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(ColTile<SHAPE>::kTile / EPT, ColTile<SHAPE>::k
   const Geo& g = kp.geo;
   const int lgG = S::lgG(g), lgN2 = S::lgN2(g);
   const int G = 1 << lgG;
-  const int col0 = blockIdx.x << lgG;
+  const int col0 = blk << lgG;
   const int tot = G << lgN2;
   const auto lay = S::lay(g);
   constexpr bool TWS = SHAPE != 0;   // static shape: stage-major twiddles in shared memory
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(ColTile<SHAPE>::kTile / EPT, ColTile<SHAPE>::k
     }
     __syncthreads();
   }
-  if constexpr (KIND == COL_GRAD_W || KIND == COL_ADMM_REV) block_accum<NT>(acc.v[0], kp.pp.gpart);
+  if constexpr (KIND == COL_GRAD_W || KIND == COL_ADMM_REV) block_accum<NT>(acc.v[0], kp.pp.gpart, blk);
   if (kp.flags & FL_STATS) {
     constexpr int kSlots =
         KIND == COL_RESIDUAL ? (1 << ST_R2)
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(ColTile<SHAPE>::kTile / EPT, ColTile<SHAPE>::k
         : (KIND == COL_ADMM || KIND == COL_ADMM_LAST) ? ((1 << ST_ERR2) | (1 << ST_DX2) | (1 << ST_X2) |
                                                          (1 << ST_L1) | (1 << ST_R2) | (1 << ST_NONFIN))
         : 0;
-    if (kSlots) block_stats<kSlots, NT>(acc, kp.pp.partials);
+    if (kSlots) block_stats<kSlots, NT>(acc, kp.pp.partials, blk);
   }
   if constexpr (E::kFwd && SHAPE != 0) {
     // static shapes: the last forward stage writes the exchange buffer itself
@@ -206,6 +207,26 @@ __global__ void __launch_bounds__(ColTile<SHAPE>::kTile / EPT, ColTile<SHAPE>::k
   }
 }
 
+template <int KIND, int SHAPE>
+__global__ void __launch_bounds__(ColTile<SHAPE>::kTile / EPT, ColTile<SHAPE>::kMinB) col_kernel(const KParams kp) {
+  col_body<KIND, SHAPE>(kp, blockIdx.x);
+}
+
+// Grouped launch over many plans (batched solves): CTA b runs tile
+// map[b].y of plan map[b].x, whose parameters kps[map[b].x] are copied to
+// shared memory first.  Run-time shapes only.
+template <int KIND>
+__global__ void __launch_bounds__(COL_TILE / EPT, COL_MINB)
+    col_kernel_multi(const KParams* __restrict__ kps, const int2* __restrict__ map) {
+  static_assert(sizeof(KParams) % 4 == 0 && sizeof(KParams) / 4 <= COL_TILE / EPT, "KParams copy");
+  __shared__ KParams skp;
+  const int2 it = map[blockIdx.x];
+  if (threadIdx.x < sizeof(KParams) / 4)
+    reinterpret_cast<int*>(&skp)[threadIdx.x] = reinterpret_cast<const int*>(kps + it.x)[threadIdx.x];
+  __syncthreads();
+  col_body<KIND, 0>(skp, it.y);
+}
+
 }  // namespace
 
 // kinds of the 2D solves (no gradient)
@@ -229,6 +250,45 @@ cudaError_t init_col_kernels() {
   CS_COL_KINDS_2D(CS_SET_COL, 3)
 #undef CS_SET_COL
   return e;
+}
+
+#define CS_COL_KINDS_MULTI(X) \
+  X(COL_LOAD) X(COL_RESIDUAL) X(COL_ISTA) X(COL_ISTA_LAST) X(COL_ADMM_INIT) X(COL_ADMM) X(COL_ADMM_LAST)
+
+cudaError_t init_col_multi_kernels() {
+  cudaError_t e = cudaSuccess;
+#define CS_SET_COLM(k) \
+  if (e == cudaSuccess) e = set_smem(col_kernel_multi<k>, COL_TILE, COL_MINB);
+  CS_COL_KINDS_MULTI(CS_SET_COLM)
+#undef CS_SET_COLM
+  return e;
+}
+
+template <typename K>
+cudaError_t launch_multi(K kern, int grid, int tile, const KParams* kps, const int2* map, cudaStream_t s,
+                         int smem_mult = 1) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(tile / EPT);
+  cfg.dynamicSmemBytes = smem_mult * pass_smem_bytes(tile);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, kps, map);
+}
+
+cudaError_t launch_col_multi(ColKind kind, const KParams* kps, const int2* map, int nctas, cudaStream_t s) {
+  if (nctas < 1) return cudaSuccess;
+#define CS_L_COLM(k) case k: return launch_multi(col_kernel_multi<k>, nctas, COL_TILE, kps, map, s);
+  switch (kind) {
+    CS_COL_KINDS_MULTI(CS_L_COLM)
+    default: break;
+  }
+#undef CS_L_COLM
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_col(ColKind kind, const KParams& kp, cudaStream_t s) {

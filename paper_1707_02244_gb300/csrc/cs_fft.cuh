@@ -176,8 +176,16 @@ struct SmemIO {
   __device__ __forceinline__ void store(int, int, float2) const {}
 };
 
+// Stage-major twiddle tables keep, for a stage of span Ls and radix R, the
+// rows r of w_{Ls R}^(r k) (k < Ls) that stage_twiddle reads: r = 1, 2, 3, 4,
+// 8, 12 for radix 16, r = 1 .. 4 for radix 8, r = 1 .. R-1 for radix 4 and 2.
+// Row `row` of a stage holds r = tw_row_r(lgR, row).
+__host__ __device__ constexpr int tw_rows(int lgR) { return lgR == 4 ? 6 : lgR == 3 ? 4 : lgR == 2 ? 3 : 1; }
+__host__ __device__ constexpr int tw_row_r(int lgR, int row) { return lgR == 4 && row >= 4 ? 4 * (row - 2) : row + 1; }
+__host__ __device__ constexpr int tw_row_of(int lgR, int r) { return lgR == 4 && r >= 8 ? r / 4 + 2 : r - 1; }
+
 // Multiply the R inputs of a butterfly by w^(r k), r = 1 .. R-1, from the
-// stage-major table block tw[(r - 1) Ls + k] = w^(r k) in shared memory.
+// stage's block tw[row(r) Ls + k] = w^(r k) of the table in shared memory.
 // Radix 16 reads r = 1, 2, 3, 4, 8, 12 and forms the other nine as
 // w^((r1 + 4 r2) k) = w^(r1 k) w^(4 r2 k); radix 8 reads r = 1 .. 4 and forms
 // r = 5 .. 7 as w^(4k) w^((r - 4) k).  Every table value is an FP64 result
@@ -185,8 +193,9 @@ struct SmemIO {
 // shared-memory reads drop from 15 to 6 (radix 16) and from 7 to 4 (radix 8).
 template <int R, int DIR>
 __device__ __forceinline__ void stage_twiddle(float2* v, const float2* __restrict__ tw, int Ls, int k) {
+  constexpr int lgR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
   auto get = [&](int r) {
-    float2 w = tw[(r - 1) * Ls + k];
+    float2 w = tw[tw_row_of(lgR, r) * Ls + k];
     if (DIR > 0) w.y = -w.y;
     return w;
   };
@@ -342,7 +351,7 @@ __device__ __forceinline__ void tile_fft(float2* s, const LAY& lay, const float2
         stockham_stage<16, DIR, TILE, NT, TWS>(s, lay, 4 * st, tws, lgLt, hook, SmemIO{}, out);
       else
         stockham_stage<16, DIR, TILE, NT, TWS>(s, lay, 4 * st, tws, lgLt, hook);
-      if (st > 0) off += 15 << (4 * st);
+      if (st > 0) off += tw_rows(4) << (4 * st);
     }
     const float2* twr = TWS ? tw + off : tw;
     if constexpr (rem == 3) stockham_stage<8, DIR, TILE, NT, TWS>(s, lay, LGL - 3, twr, lgLt, hook, SmemIO{}, out);
@@ -368,12 +377,12 @@ __device__ __forceinline__ void tile_fft(float2* s, const LAY& lay, const float2
 }
 
 // Entries of the stage-major twiddle table of a length-L FFT: stage s >= 1
-// (span Ls, radix R) contributes (R - 1) * Ls entries.
+// (span Ls, radix R) contributes tw_rows(log2 R) * Ls entries.
 __host__ __device__ constexpr int stage_tw_count(int lgL) {
   int n = 0, lgLs = 0;
   while (lgLs < lgL) {
     const int lgR = (lgL - lgLs) >= 4 ? 4 : (lgL - lgLs);
-    if (lgLs > 0) n += ((1 << lgR) - 1) << lgLs;
+    if (lgLs > 0) n += tw_rows(lgR) << lgLs;
     lgLs += lgR;
   }
   return n;

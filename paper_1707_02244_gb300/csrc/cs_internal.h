@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct cs_plan_s;
+
 namespace csk {
 
 // Four-step geometry of one complex FFT of length N = N1 * N2, stored as an
@@ -131,6 +133,13 @@ size_t pass_smem_bytes(int tile);
 cudaError_t init_pass_kernels();
 cudaError_t init_col_kernels();
 cudaError_t init_mid_kernels();
+// Grouped launches over many plans (batched solves, run-time shapes,
+// 4096-value tiles): CTA b runs tile map[b].y of the plan whose parameters
+// are kps[map[b].x] (both device arrays).
+cudaError_t launch_col_multi(ColKind kind, const KParams* kps, const int2* map, int nctas, cudaStream_t s);
+cudaError_t launch_mid_multi(MidKind kind, const KParams* kps, const int2* map, int nctas, cudaStream_t s);
+cudaError_t init_col_multi_kernels();
+cudaError_t init_mid_multi_kernels();
 
 // Small kernels (cs_aux.cu).
 cudaError_t launch_set_args(const CallArgs& a, CallArgs* dst, cudaStream_t s);
@@ -182,6 +191,41 @@ cudaError_t launch_norm2(const float* x, int64_t n, double* partials, double* ou
 cudaError_t launch_power_init(float* u, int64_t n, cudaStream_t s);
 // out[0] = scale * sum(v[0 .. count)), summed in a fixed order in FP64.
 cudaError_t launch_sum_scaled(const double* v, int count, float scale, float* out, cudaStream_t s);
+
+// One plan of a grouped (batched) solve: what the grouped element-wise
+// kernels need of it.
+struct GroupDesc {
+  Geo gi, ga;                  // real-FFT and complex-n geometry
+  int64_t noff, moff, m;       // offsets of its x / z and y in the concatenated vectors; rows kept
+  const int32_t* pos_i;        // compact position of y[i], real-FFT geometry
+  float* ys_i;
+  const int32_t* pos_a;        // the same, complex-n geometry
+  float* ys_a;
+  float* xi_t;                 // ISTA iterate (tile order of gi, float2[n/2])
+  float *av, *az, *amu, *anu;  // ADMM state (tile order of ga)
+};
+
+// The plan's parameters of the pass kernels (flags 0, its own CallArgs), its
+// geometries and buffers, for grouped launches (cs_api.cu).
+struct PlanView {
+  KParams kp_i, kp_a;          // real-FFT and complex-n geometry
+  GroupDesc desc;
+};
+PlanView plan_view(cs_plan_s* p);
+// Re-tabulate the plan's ADMM inverse spectrum for (rho, sigma) when it holds
+// another pair.
+cudaError_t plan_admm_table(cs_plan_s* p, double rho, double sigma, cudaStream_t s);
+
+// Grouped element-wise kernels over `count` plans (cs_aux.cu): compact y of
+// every plan (geometry: 0 real-FFT, 1 complex-n; non-finite values latch
+// STS_NONFINITE in *status); x (natural order) to and from the ISTA iterates;
+// the zero ADMM state; z from the ADMM state.
+cudaError_t launch_group_scatter_y(const GroupDesc* d, int count, const float* y, int geo, int* status,
+                                   cudaStream_t s);
+cudaError_t launch_group_ista_in(const GroupDesc* d, int count, const float* x, cudaStream_t s);
+cudaError_t launch_group_ista_out(const GroupDesc* d, int count, float* x, cudaStream_t s);
+cudaError_t launch_group_admm_zero(const GroupDesc* d, int count, cudaStream_t s);
+cudaError_t launch_group_admm_out(const GroupDesc* d, int count, float* z, cudaStream_t s);
 
 // Device status bits.
 enum : int { STS_NONFINITE = 1, STS_TIMEOUT = 2, STS_BAD_ROW = 4, STS_DUP_ROW = 8 };

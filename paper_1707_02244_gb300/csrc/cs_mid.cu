@@ -162,8 +162,9 @@ template <> struct MidShape<4> : MidShape<0> { static constexpr bool kTwoD = tru
 template <> struct MidShape<5> : MidShapeS<11, 0, true> {};
 template <> struct MidShape<6> : MidShapeS<12, 0, true> {};
 
+// The mid pass of tile `blk` (row-pair units blk U .. blk U + U - 1).
 template <int KIND, int TILE, int SHAPE>
-__global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(const KParams kp) {
+__device__ __forceinline__ void mid_body(const KParams& kp, const int blk) {
   constexpr int NT = Cfg<TILE>::NT;
   constexpr int NLD = Cfg<TILE>::NLD;
   using S = MidShape<SHAPE>;
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
   pdl_trigger();
   const Geo& g = kp.geo;
   const int lgU = S::lgU(g), U = 1 << lgU;
-  const int u0 = blockIdx.x << lgU;
+  const int u0 = blk << lgU;
   const int lgN1 = S::lgN1(g), N1 = 1 << lgN1;
   const int tot = (2 * U) << lgN1;
   const auto lay = S::lay(g);
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
     }
     // spectrum operator over all (k, N-k) pairs held by this CTA (unrolled so
     // that the table loads of several slots are in flight together)
-#pragma unroll 4
+#pragma unroll 8
     for (int t = threadIdx.x; t < nslots; t += NT) {
       int ea, eb, k2, k1, tidx;
       slot_at(t, ea, eb, k2, k1, tidx);
@@ -474,6 +475,25 @@ __global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(con
       __stcg(reinterpret_cast<float4*>(W + ((size_t)k2 << lgN1) + j1), make_float4(lo.x, lo.y, hi.x, hi.y));
     }
   }
+}
+
+template <int KIND, int TILE, int SHAPE>
+__global__ void __launch_bounds__(Cfg<TILE>::NT, Cfg<TILE>::MINB) mid_kernel(const KParams kp) {
+  mid_body<KIND, TILE, SHAPE>(kp, blockIdx.x);
+}
+
+// Grouped launch over many plans (batched solves): CTA b runs tile
+// map[b].y of plan map[b].x (4096-value tiles, run-time shapes).
+template <int KIND>
+__global__ void __launch_bounds__(Cfg<4096>::NT, Cfg<4096>::MINB)
+    mid_kernel_multi(const KParams* __restrict__ kps, const int2* __restrict__ map) {
+  static_assert(sizeof(KParams) % 4 == 0 && sizeof(KParams) / 4 <= Cfg<4096>::NT, "KParams copy");
+  __shared__ KParams skp;
+  const int2 it = map[blockIdx.x];
+  if (threadIdx.x < sizeof(KParams) / 4)
+    reinterpret_cast<int*>(&skp)[threadIdx.x] = reinterpret_cast<const int*>(kps + it.x)[threadIdx.x];
+  __syncthreads();
+  mid_body<KIND, 4096, 0>(skp, it.y);
 }
 
 }  // namespace
@@ -535,9 +555,43 @@ cudaError_t launch_mid(MidKind kind, const KParams& kp, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+#define CS_MID_KINDS_MULTI(X) X(MID_FWD) X(MID_ADJ) X(MID_ADMM)
+
+cudaError_t init_mid_multi_kernels() {
+  cudaError_t e = cudaSuccess;
+#define CS_SET_MIDM(k) \
+  if (e == cudaSuccess) e = set_smem(mid_kernel_multi<k>, 4096, Cfg<4096>::MINB);
+  CS_MID_KINDS_MULTI(CS_SET_MIDM)
+#undef CS_SET_MIDM
+  return e;
+}
+
+cudaError_t launch_mid_multi(MidKind kind, const KParams* kps, const int2* map, int nctas, cudaStream_t s) {
+  if (nctas < 1) return cudaSuccess;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(nctas);
+  cfg.blockDim = dim3(Cfg<4096>::NT);
+  cfg.dynamicSmemBytes = pass_smem_bytes(4096);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  switch (kind) {
+    case MID_FWD: return cudaLaunchKernelEx(&cfg, mid_kernel_multi<MID_FWD>, kps, map);
+    case MID_ADJ: return cudaLaunchKernelEx(&cfg, mid_kernel_multi<MID_ADJ>, kps, map);
+    case MID_ADMM: return cudaLaunchKernelEx(&cfg, mid_kernel_multi<MID_ADMM>, kps, map);
+    default: break;
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t init_pass_kernels() {
   cudaError_t e = init_col_kernels();
-  return e == cudaSuccess ? init_mid_kernels() : e;
+  if (e == cudaSuccess) e = init_mid_kernels();
+  if (e == cudaSuccess) e = init_col_multi_kernels();
+  return e == cudaSuccess ? init_mid_multi_kernels() : e;
 }
 
 size_t pass_smem_bytes(int tile) { return sizeof(float2) * (size_t)smem_slots(tile); }

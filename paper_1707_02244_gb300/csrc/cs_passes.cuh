@@ -55,7 +55,7 @@ struct Acc {
 // Block reduction of the per-thread accumulators into partials[block].
 // Deterministic: fixed shuffle tree, fixed warp order.  SLOTS is a bit mask.
 template <int SLOTS, int NT>
-__device__ void block_stats(const Acc& a, double* partials) {
+__device__ void block_stats(const Acc& a, double* partials, int blk) {
   __shared__ double red[NT / 32][NSTAT];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -70,7 +70,7 @@ __device__ void block_stats(const Acc& a, double* partials) {
   if (threadIdx.x < NSTAT && ((SLOTS >> threadIdx.x) & 1)) {
     double s = 0.0;
     for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
-    partials[blockIdx.x * NSTAT + threadIdx.x] = s;
+    partials[blk * NSTAT + threadIdx.x] = s;
   }
 }
 
@@ -104,10 +104,10 @@ template <int KIND> struct UsesMask {
                                  KIND == COL_ADMM_REV) ? 1 : 0;
 };
 
-// Block sum of one per-thread value, added to dst[blockIdx.x] (one slot per
-// CTA, so repeated launches accumulate without atomics; fixed order).
+// Block sum of one per-thread value, added to dst[blk] (one slot per tile,
+// so repeated launches accumulate without atomics; fixed order).
 template <int NT>
-__device__ void block_accum(float v, double* dst) {
+__device__ void block_accum(float v, double* dst, int blk) {
   __shared__ double red[NT / 32];
   double d = (double)v;
 #pragma unroll
@@ -117,7 +117,7 @@ __device__ void block_accum(float v, double* dst) {
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < NT / 32; ++w) s += red[w];
-    dst[blockIdx.x] += s;
+    dst[blk] += s;
   }
 }
 

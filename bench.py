@@ -31,10 +31,13 @@ The profile-* workloads are short fixed launch sequences for ncu captures
   profile-grad    n = 2^20, m = n/4, 4 unrolled ISTA steps, checkpoints every 2.
 
 The batched workload: 512 independent instances, n log-uniform in
-[2^12, 2^20] (snapped to powers of two), m/n uniform in [0.2, 0.5], k/n =
-0.01, each with its own c; one step = T ISTA + T ADMM iterations of every
-instance through cs_batch_*, against the same work done by looping the plain
-per-instance solver (cs_ista / cs_admm on one plan per instance).
+[2^12, 2^20] snapped to the nearest 7-smooth integer (--sizes smooth, the
+default; --sizes pow2 snaps to powers of two), m/n uniform in [0.2, 0.5],
+k/n = 0.01, each with its own c; y = A x* + noise and tau = 1/max|c^|^2 are
+synthesised with torch.fft in FP64.  One step = T ISTA + T ADMM iterations
+of every instance through cs_batch_*, against the same work done one
+instance at a time (7-smooth: a one-instance batch per instance; powers of
+two: the plain solver, cs_ista / cs_admm on one plan per instance).
 
 Under torchrun each rank solves its own instance (replicas, no collective on
 the data path) and rank 0 prints one JSON line.
@@ -78,6 +81,8 @@ def parse():
                     choices=["n2e22", "batched", "grad", "context", "deblur2d",
                              "profile-iter", "profile-passes", "profile-batch", "profile-2d", "profile-grad"])
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched workload")
+    ap.add_argument("--sizes", default="smooth", choices=["smooth", "pow2"],
+                    help="batched workload: n snapped to 7-smooth integers or to powers of two")
     return ap.parse_args()
 
 
@@ -487,9 +492,9 @@ def time_to_nmse(cs, plan, y, xt, tau, n, dev, torch):
 
 
 def run_batched(args):
-    """Batched solves against looping the plain solver (see the module
-    docstring); 1 GPU, device-timed with CUDA events, L2 flushed between
-    steps."""
+    """Batched solves against solving the instances one at a time (see the
+    module docstring); 1 GPU, device-timed with CUDA events, L2 flushed
+    between steps."""
     import torch
     import paper_1707_02244_gb300 as cs
 
@@ -497,27 +502,34 @@ def run_batched(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     T = args.iters
-    n, m = synth.batch_sizes(args.batch, 12, 20, synth.BATCH_SEED)
+    n, m = synth.batch_sizes(args.batch, 12, 20, synth.BATCH_SEED, snap=args.sizes)
     insts = synth.batch_instances(n, m)
     noff = np.concatenate([[0], np.cumsum(n)[:-1]])
     moff = np.concatenate([[0], np.cumsum(m)[:-1]])
     N, M = int(n.sum()), int(m.sum())
-    t0 = time.perf_counter()
-    plans = [cs.cs_plan(i.n, i.m, i.rows, i.c, stream) for i in insts]
-    plans_s = time.perf_counter() - t0
+    # inputs: y = S C x* + noise and tau = 1 / max |c^|^2 (>= 1 / ||A||^2), FP64 torch.fft
     xt = torch.from_numpy(np.concatenate([i.x_true for i in insts]).astype(np.float32)).to(dev)
-    y = torch.empty(M, dtype=torch.float32, device=dev)
-    taus = np.empty(len(insts), dtype=np.float32)
-    for j, p in enumerate(plans):
-        cs.cs_forward(p, xt[noff[j]:noff[j] + n[j]], y[moff[j]:moff[j] + m[j]])
-        taus[j] = np.float32(1.0 / cs.cs_opnorm2(p, 30))
-    y += torch.from_numpy(np.concatenate([i.noise for i in insts]).astype(np.float32)).to(dev)
+    ys, taus = [], np.empty(len(insts), dtype=np.float32)
+    for j, inst in enumerate(insts):
+        ch = torch.fft.fft(torch.from_numpy(inst.c).to(dev))
+        cx = torch.fft.ifft(torch.conj(ch) * torch.fft.fft(torch.from_numpy(inst.x_true).to(dev))).real
+        ys.append(cx[torch.from_numpy(inst.rows).to(dev)] + torch.from_numpy(inst.noise).to(dev))
+        taus[j] = np.float32(1.0 / float((ch.abs() ** 2).max()))
+    y = torch.cat(ys).to(torch.float32)
+    del ys
+    rows_all, c_all = np.concatenate([i.rows for i in insts]), np.concatenate([i.c for i in insts])
     t0 = time.perf_counter()
-    batch = cs.cs_batch_plan(n, m, np.concatenate([i.rows for i in insts]), np.concatenate([i.c for i in insts]),
-                             stream)
+    batch = cs.cs_batch_plan(n, m, rows_all, c_all, stream)
     batch_plan_s = time.perf_counter() - t0
     lam = np.full(len(insts), LAM, dtype=np.float32)
     rho = np.full(len(insts), RHO, dtype=np.float32)
+    # one at a time: plans (powers of two) or one-instance batches
+    t0 = time.perf_counter()
+    if args.sizes == "pow2":
+        singles = [cs.cs_plan(i.n, i.m, i.rows, i.c, stream) for i in insts]
+    else:
+        singles = [cs.cs_batch_plan([i.n], [i.m], i.rows, i.c, stream) for i in insts]
+    singles_s = time.perf_counter() - t0
     xb = torch.zeros(N, dtype=torch.float32, device=dev)
     zb = torch.zeros(N, dtype=torch.float32, device=dev)
     xl = torch.zeros(N, dtype=torch.float32, device=dev)
@@ -529,12 +541,21 @@ def run_batched(args):
         cs.cs_batch_ista(batch, y, lam, taus, T, xb)
         cs.cs_batch_admm(batch, y, lam, rho, T, zb)
 
-    def looped():
-        xl.zero_()
-        for j, p in enumerate(plans):
+    def one_at_a_time(ista=True, admm=True, iters=T):
+        if ista:
+            xl.zero_()
+        for j, p in enumerate(singles):
             sl, sm = slice(noff[j], noff[j] + n[j]), slice(moff[j], moff[j] + m[j])
-            cs.cs_ista(p, y[sm], LAM, float(taus[j]), T, xl[sl], stats=False)
-            cs.cs_admm(p, y[sm], LAM, RHO, T, zl[sl], stats=False)
+            if args.sizes == "pow2":
+                if ista:
+                    cs.cs_ista(p, y[sm], LAM, float(taus[j]), iters, xl[sl], stats=False)
+                if admm:
+                    cs.cs_admm(p, y[sm], LAM, RHO, iters, zl[sl], stats=False)
+            else:
+                if ista:
+                    cs.cs_batch_ista(p, y[sm], lam[j:j + 1], taus[j:j + 1], iters, xl[sl])
+                if admm:
+                    cs.cs_batch_admm(p, y[sm], lam[j:j + 1], rho[j:j + 1], iters, zl[sl])
 
     def timed(fn, steps):
         for _ in range(args.warmup):
@@ -554,7 +575,7 @@ def run_batched(args):
     clocks = Clocks(0)
     clocks.start()
     ms_b = timed(batched, args.steps)
-    ms_l = timed(looped, max(3, args.steps // 5)) if not args.no_extras else float("nan")
+    ms_l = timed(one_at_a_time, max(3, args.steps // 5)) if not args.no_extras else float("nan")
     clk = clocks.stop()
     assert cs.cs_batch_status_sync(batch) == cs.CS_OK
 
@@ -570,7 +591,7 @@ def run_batched(args):
 
     # time to NMSE 1e-4: the ADMM iteration count at which the instances
     # reach it (doubling from 100, at most 1600), the batched solve timed at
-    # that count, the looped solve from its measured per-iteration cost
+    # that count, the one-at-a-time solve from its measured per-iteration cost
     def admm_batched(iters):
         a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         zz = torch.zeros(N, dtype=torch.float32, device=dev)
@@ -590,41 +611,44 @@ def run_batched(args):
         if frac >= 0.95:
             break
     if not args.no_extras:
-        zl.zero_()
         a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for j, p in enumerate(plans):
-            cs.cs_admm(p, y[moff[j]:moff[j] + m[j]], LAM, RHO, T, zl[noff[j]:noff[j] + n[j]], stats=False)
+        one_at_a_time(ista=False, admm=True)
         b2.record(stream)
         torch.cuda.synchronize()
-        looped_admm_ms_per_iter = a.elapsed_time(b2) / T
-        ttn["looped_ms_est"] = looped_admm_ms_per_iter * ttn["admm_iters"]
-        ttn["speedup"] = ttn["looped_ms_est"] / ttn["batched_ms"]
-    classes = {int(k): int(v) for k, v in zip(*np.unique(n, return_counts=True))}
+        ttn["one_at_a_time_ms_est"] = a.elapsed_time(b2) / T * ttn["admm_iters"]
+        ttn["speedup"] = ttn["one_at_a_time_ms_est"] / ttn["batched_ms"]
+    pow2 = (n & (n - 1)) == 0
+    paths = {"pow2_single_cta": int(np.sum(pow2 & (n <= 8192))), "pow2_grouped": int(np.sum(pow2 & (n > 8192))),
+             "smooth_single_cta": int(np.sum(~pow2 & (n <= 4096))),
+             "smooth_four_step": int(np.sum(~pow2 & (n > 4096)))}
     line = {
-        "metric": "batched ISTA+ADMM instance-iterations/s (512 uneven instances) vs looping the plain solver",
+        "metric": "batched ISTA+ADMM instance-iterations/s (512 uneven instances) vs solving them one at a time",
         "value": len(insts) * 2 * T / (ms_b / 1e3), "unit": "instance-iter/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batched: {len(insts)} instances, n log-uniform [2^12, 2^20] snapped to powers "
-                               "of two, m/n uniform [0.2, 0.5], k/n=0.01, noise 1e-3, own c each; "
-                               f"lambda={LAM}, tau=1/||A_i||^2 (GPU power iteration), rho={RHO}",
-                   "iters_per_solver_per_step": T, "sum_n": N, "sum_m": M, "size_classes": classes,
+        "config": {"workload": f"batched: {len(insts)} instances, n log-uniform [2^12, 2^20] snapped to "
+                               f"{'7-smooth integers' if args.sizes == 'smooth' else 'powers of two'}, "
+                               "m/n uniform [0.2, 0.5], k/n=0.01, noise 1e-3, own c each; "
+                               f"lambda={LAM}, tau=1/max|c^|^2, rho={RHO}",
+                   "iters_per_solver_per_step": T, "sum_n": N, "sum_m": M, "paths": paths,
+                   "distinct_n": int(len(np.unique(n))),
                    "l2": "flushed (512 MiB write) between steps, outside the timed events"},
         "element_iter_per_s": N * 2 * T / (ms_b / 1e3),
-        "looped": {"ms_per_step": ms_l, "value": len(insts) * 2 * T / (ms_l / 1e3),
-                   "element_iter_per_s": N * 2 * T / (ms_l / 1e3)},
-        "speedup_vs_looped": ms_l / ms_b,
+        "one_at_a_time": {"how": "plain plan per instance" if args.sizes == "pow2" else "one-instance batch per instance",
+                          "ms_per_step": ms_l, "value": len(insts) * 2 * T / (ms_l / 1e3),
+                          "element_iter_per_s": N * 2 * T / (ms_l / 1e3)},
+        "speedup_vs_one_at_a_time": ms_l / ms_b,
         "admm_nmse_vs_xtrue_after_T": {"batched_median": float(np.median(nb)), "batched_max": float(nb.max()),
-                                       "looped_median": float(np.median(nl)), "looped_max": float(nl.max())},
+                                       "one_at_a_time_median": float(np.median(nl)),
+                                       "one_at_a_time_max": float(nl.max())},
         "time_to_nmse_1e-4": ttn,
-        "plan_s": {"batch": batch_plan_s, "per_instance_plans": plans_s},
-        "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
+        "plan_s": {"batch": batch_plan_s, "one_at_a_time": singles_s},
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     batch.close()
-    for p in plans:
+    for p in singles:
         p.close()
     return 0
 

@@ -10,7 +10,11 @@
  *
  * Conventions shared by every call
  *   - Vectors passed to a call are DEVICE pointers to fp32 arrays on the
- *     current device, used on the stream given to cs_plan.  Calls are
+ *     current device, used on the stream given to cs_plan.  The n-vectors
+ *     of cs_forward, cs_adjoint, cs_ista, cs_set_monitor and the gradient
+ *     calls are 8-byte aligned (CS_ERR_ARG otherwise); every other vector,
+ *     and the batch calls' concatenations, may start at any 4-byte offset.
+ *     Calls are
  *     asynchronous with respect to the host unless a cs_stats pointer is
  *     passed (then the call waits for its own work to finish).
  *   - y[i] always pairs with row rows[i] as given to cs_plan (any order).
@@ -217,23 +221,34 @@ cs_status cs_grad_admm(cs_plan_t plan, const float* y, float lambda, const cs_ad
 /* ---------------------------------------------------------------------
  * Batched solves (no counterpart in the paper; its recovery problem solved
  * for many independent instances at once).  Instance i has its own n_i,
- * m_i, rows and c.  Instances with n_i <= CS_BATCH_MAX_N are solved one CTA
- * per instance, the iterate kept in shared memory for all iterations (one
- * launch per power-of-two size class, on up to 4 internal streams forked
- * from the batch's stream).  Larger instances each have the buffers and
- * tables of a plan, but are iterated together: every pass of an iteration
- * is one launch over the tiles of all of them, so their whole solve is one
- * CUDA graph launch on the batch's stream.
+ * m_i, rows and c.  Three solvers share a call:
+ *   - power-of-two n_i <= CS_BATCH_MAX_N: one CTA per instance, the iterate
+ *     kept in shared memory for all iterations (one launch per size class,
+ *     on up to 4 internal streams forked from the batch's stream);
+ *   - larger power-of-two n_i: the buffers and tables of a plan, iterated
+ *     together (every pass of an iteration is one launch over the tiles of
+ *     all of them; their whole solve is one CUDA graph launch);
+ *   - 7-smooth n_i = 2^a 3^b 5^c 7^d that is not a power of two: mixed-radix
+ *     FFTs (radices 8, 4, 2, 7, 5, 3), one CTA per instance up to n_i = 4096,
+ *     above it a four-step split n_i = N1 N2 chosen by a plan-time tuner
+ *     (cached per n for the process; the environment variable
+ *     CS_BATCH_AUTOTUNE=0 keeps the heuristic split).  All of these
+ *     instances are solved by ONE persistent launch per call whose CTAs take
+ *     (instance, pass, tile) items from a device-side queue; a tile waits,
+ *     bounded, for its instance's previous pass (CS_ERR_TIMEOUT from
+ *     cs_batch_status_sync if a wait ran out).
+ * The concatenated vectors may hold instances of odd length: any 4-byte
+ * offset is accepted.
  * --------------------------------------------------------------------- */
 #define CS_BATCH_MAX_N 8192
 typedef struct cs_batch_s* cs_batch_t;
 
 /*   count     number of instances (>= 1)
- *   n, m      HOST int64[count]: n_i power of two, 64 <= n_i <= 2^21;
- *             1 <= m_i <= n_i
+ *   n, m      HOST int64[count]: n_i a power of two with 64 <= n_i <= 2^21,
+ *             or 7-smooth with 16 <= n_i <= 2^20; 1 <= m_i <= n_i
  *   rows      HOST int64[sum m_i]: instance i's rows, concatenated
  *   c         HOST float64[sum n_i]: instance i's first row of C, concatenated
- * Synchronises.  Errors as cs_plan. */
+ * Synchronises.  Errors as cs_plan; CS_ERR_UNSUPPORTED for any other n_i. */
 cs_status cs_batch_plan(cs_batch_t* out, int count, const int64_t* n, const int64_t* m,
                         const int64_t* rows, const double* c, void* stream);
 cs_status cs_batch_destroy(cs_batch_t batch);
@@ -252,9 +267,11 @@ cs_status cs_batch_ista(cs_batch_t batch, const float* y, const float* lambda,
 cs_status cs_batch_admm(cs_batch_t batch, const float* y, const float* lambda,
                         const float* rho, int iters, float* z);
 
-/* Waits for the batch's work; returns CS_ERR_NONFINITE if a measurement was
- * not finite, else the first error latched by a per-instance plan.  The
- * latched status is cleared (each condition is reported once). */
+/* Waits for the batch's work; returns the first error latched by a
+ * per-instance plan, else CS_ERR_TIMEOUT if a bounded wait of the
+ * mixed-radix solver ran out, else CS_ERR_NONFINITE if a measurement was
+ * not finite.  The latched status is cleared (each condition is reported
+ * once). */
 cs_status cs_batch_status_sync(cs_batch_t batch);
 
 /* Direct circulant product (context comparator; Sec. 5.2's scheme of one

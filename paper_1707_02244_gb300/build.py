@@ -13,7 +13,7 @@ ROOT = PKG.parent
 SRC = PKG / "csrc"
 OBJ = PKG / "_build"
 LIB = PKG / "libcsgb.so"
-SOURCES = ["cs_col.cu", "cs_mid.cu", "cs_aux.cu", "cs_api.cu", "cs_static.cu", "cs_batch.cu", "cs_direct.cu"]
+SOURCES = ["cs_col.cu", "cs_mid.cu", "cs_aux.cu", "cs_api.cu", "cs_static.cu", "cs_batch.cu", "cs_smooth.cu", "cs_direct.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", str(ROOT / "include")]
 

@@ -245,6 +245,25 @@ __global__ void from_tile_k(const T* __restrict__ tiled, T* __restrict__ nat, Ge
   if (t < g.N) nat[tile_to_nat(g, t)] = tiled[t];
 }
 
+// The same for complex elements of a caller's float vector that starts on a
+// 4-byte (not 8-byte) boundary: two 4-byte accesses per element.
+__global__ void to_tile_pair_k(const float* __restrict__ nat, float2* __restrict__ tiled, Geo g) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= g.N) return;
+  const int64_t p = tile_to_nat(g, t);
+  tiled[t] = make_float2(nat[2 * p], nat[2 * p + 1]);
+}
+__global__ void from_tile_pair_k(const float2* __restrict__ tiled, float* __restrict__ nat, Geo g) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= g.N) return;
+  const int64_t p = tile_to_nat(g, t);
+  const float2 v = tiled[t];
+  nat[2 * p] = v.x;
+  nat[2 * p + 1] = v.y;
+}
+
+inline bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
 // Exclusive prefix count of set bits per 32-bit word, one CTA.
 __global__ void __launch_bounds__(1024) prefix_k(const uint32_t* __restrict__ mask, int64_t words,
                                                  uint32_t* __restrict__ prefix) {
@@ -460,7 +479,9 @@ cudaError_t launch_build_mask(const int64_t* rows, int64_t m, int64_t n, const G
 }
 
 cudaError_t launch_to_tile(const void* nat, void* tiled, const Geo& g, int complex_elems, cudaStream_t s) {
-  if (complex_elems)
+  if (complex_elems && !aligned8(nat))
+    to_tile_pair_k<<<blocks_for(g.N), AUX_NT, 0, s>>>((const float*)nat, (float2*)tiled, g);
+  else if (complex_elems)
     to_tile_k<float2><<<blocks_for(g.N), AUX_NT, 0, s>>>((const float2*)nat, (float2*)tiled, g);
   else
     to_tile_k<float><<<blocks_for(g.N), AUX_NT, 0, s>>>((const float*)nat, (float*)tiled, g);
@@ -468,7 +489,9 @@ cudaError_t launch_to_tile(const void* nat, void* tiled, const Geo& g, int compl
 }
 
 cudaError_t launch_from_tile(const void* tiled, void* nat, const Geo& g, int complex_elems, cudaStream_t s) {
-  if (complex_elems)
+  if (complex_elems && !aligned8(nat))
+    from_tile_pair_k<<<blocks_for(g.N), AUX_NT, 0, s>>>((const float2*)tiled, (float*)nat, g);
+  else if (complex_elems)
     from_tile_k<float2><<<blocks_for(g.N), AUX_NT, 0, s>>>((const float2*)tiled, (float2*)nat, g);
   else
     from_tile_k<float><<<blocks_for(g.N), AUX_NT, 0, s>>>((const float*)tiled, (float*)nat, g);
@@ -492,11 +515,17 @@ __global__ void group_scatter_y_k(const GroupDesc* __restrict__ d, const float* 
 template <bool IN>
 __global__ void group_ista_k(const GroupDesc* __restrict__ d, float* x) {
   const GroupDesc& g = d[blockIdx.y];
-  float2* xn = reinterpret_cast<float2*>(x + g.noff);
+  float* xn = x + g.noff;   // 4-byte aligned only: the concatenation may hold odd-length instances
   float2* xt = reinterpret_cast<float2*>(g.xi_t);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.gi.N; t += (int64_t)gridDim.x * blockDim.x) {
-    if (IN) xt[t] = xn[tile_to_nat(g.gi, t)];
-    else xn[tile_to_nat(g.gi, t)] = xt[t];
+    const int64_t p = tile_to_nat(g.gi, t);
+    if (IN) {
+      xt[t] = make_float2(xn[2 * p], xn[2 * p + 1]);
+    } else {
+      const float2 v = xt[t];
+      xn[2 * p] = v.x;
+      xn[2 * p + 1] = v.y;
+    }
   }
 }
 

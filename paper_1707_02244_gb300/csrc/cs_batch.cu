@@ -7,7 +7,9 @@
 // pass of an iteration is one grouped launch over the tiles of all of them
 // (col_kernel_multi / mid_kernel_multi), so a whole solve of every large
 // instance is one captured CUDA graph on the batch's stream, ordered by the
-// kernel boundaries alone.
+// kernel boundaries alone.  Instances whose n is 7-smooth but not a power of
+// two go to the mixed-radix solver of cs_smooth.cu (one persistent launch per
+// solve over all of them).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -102,14 +104,14 @@ __global__ void __launch_bounds__((1 << LG) / EPT) batch_ista_k(
   const int id = order[blockIdx.x];
   const BatchDesc d = descs[id];
   const BatchScalars s = sc[id];
-  float2* xg = reinterpret_cast<float2*>(x + d.noff);
+  float* xg = x + d.noff;   // 4-byte aligned only: the concatenation may hold odd-length instances
   const uint32_t* mk = mask + d.woff;
   const uint32_t* pf = prefix + d.woff;
   const float* yv = ys + d.moff;
   const float4* tAi = tA + d.itab;
   const float2* tBi = tB + d.itab;
   for (int p = threadIdx.x; p < N; p += NT) {
-    const float2 v = xg[p];
+    const float2 v = make_float2(xg[2 * p], xg[2 * p + 1]);
     X[p] = v;
     S[pad(p)] = v;
   }
@@ -140,7 +142,10 @@ __global__ void __launch_bounds__((1 << LG) / EPT) batch_ista_k(
     }
     __syncthreads();
   }
-  for (int p = threadIdx.x; p < N; p += NT) xg[p] = X[p];
+  for (int p = threadIdx.x; p < N; p += NT) {
+    xg[2 * p] = X[p].x;
+    xg[2 * p + 1] = X[p].y;
+  }
 }
 
 // One CTA solves instance order[blockIdx.x] (n = 2^LG) for `iters`
@@ -340,6 +345,8 @@ struct cs_batch_s {
   std::vector<int64_t> n, m, noff, moff;
   std::vector<int> small;           // instances solved by the single-CTA kernels, largest first
   std::vector<int> large;           // instances solved by their own plan
+  std::vector<int> smooth_ids;      // 7-smooth, not power-of-two n: the mixed-radix solver
+  SmoothSet* smooth = nullptr;
   std::vector<cs_plan_t> plans;     // per large instance
   // grouped launches over the large instances (in the order of `large`)
   struct Group {
@@ -389,6 +396,7 @@ void batch_free(cs_batch_s* b) {
   if (!b) return;
   for (cs_plan_t p : b->plans)
     if (p) cs_plan_destroy(p);
+  smooth_free(b->smooth);
   void* bufs[] = {b->descs, b->sc,   b->order,  b->tA,  b->tB, b->tc, b->abs2, b->tb,  b->tb_inst,
                   b->drho,  b->dsigma, b->mask, b->prefix, b->pos, b->ys, b->tw, b->amu, b->anu, b->status};
   for (void* q : bufs)
@@ -507,7 +515,8 @@ cs_status cs_batch_plan(cs_batch_t* out, int count, const int64_t* n, const int6
   if (!out || count < 1 || !n || !m || !rows || !c) return CS_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
-    if (n[i] < 64 || n[i] > (int64_t(1) << 21) || !pow2(n[i])) return CS_ERR_UNSUPPORTED;
+    const bool p2 = pow2(n[i]) && n[i] >= 64 && n[i] <= (int64_t(1) << 21);
+    if (!p2 && !smooth_size(n[i])) return CS_ERR_UNSUPPORTED;
     if (m[i] < 1 || m[i] > n[i]) return CS_ERR_ARG;
   }
   cs_batch_s* b = new (std::nothrow) cs_batch_s();
@@ -537,7 +546,9 @@ cs_status cs_batch_plan(cs_batch_t* out, int count, const int64_t* n, const int6
     d.atab = at;
     no += n[i];
     mo += m[i];
-    if (n[i] <= CS_BATCH_MAX_N) {
+    if (!pow2(n[i])) {
+      b->smooth_ids.push_back(i);
+    } else if (n[i] <= CS_BATCH_MAX_N) {
       b->small.push_back(i);
       wo += n[i] / 32;
       it += n[i] / 4 + 1;
@@ -735,6 +746,11 @@ cs_status cs_batch_plan(cs_batch_t* out, int count, const int64_t* n, const int6
     CS_B_TRY(balloc(&b->status, 1));
     CS_B_TRY(cudaMemsetAsync(b->status, 0, sizeof(int), s));
   }
+  if (!b->smooth_ids.empty()) {
+    const cs_status st = (cs_status)smooth_plan(&b->smooth, b->smooth_ids.data(), (int)b->smooth_ids.size(), n, m,
+                                                b->noff.data(), b->moff.data(), rows, c, b->status, s);
+    if (st != CS_OK) return fail(st);
+  }
   CS_B_TRY(cudaStreamSynchronize(s));
   for (int k = 0; k < b->nside; ++k) CS_B_TRY(cudaStreamSynchronize(b->side[k]));
 #undef CS_B_TRY
@@ -801,6 +817,7 @@ cs_status cs_batch_ista(cs_batch_t b, const float* y, const float* lambda, const
     }
   }
   const cs_status sj = cstat(join_sides(b));
+  if (st == CS_OK && sj == CS_OK && b->smooth) st = cstat(smooth_ista(b->smooth, y, lambda, tau, iters, x, s));
   return st != CS_OK ? st : sj;
 }
 
@@ -888,6 +905,7 @@ cs_status cs_batch_admm(cs_batch_t b, const float* y, const float* lambda, const
     }
   }
   const cs_status sj = cstat(join_sides(b));
+  if (st == CS_OK && sj == CS_OK && b->smooth) st = cstat(smooth_admm(b->smooth, y, lambda, rho, iters, z, s));
   return st != CS_OK ? st : sj;
 }
 
@@ -905,6 +923,7 @@ cs_status cs_batch_status_sync(cs_batch_t b) {
     if (st != CS_OK) return st;
     st = cstat(cudaMemset(b->status, 0, sizeof(int)));   // reported once, as cs_status_sync
     if (st != CS_OK) return st;
+    if (hs & STS_TIMEOUT) return CS_ERR_TIMEOUT;
     if (hs & STS_NONFINITE) return CS_ERR_NONFINITE;
   }
   return CS_OK;

@@ -230,4 +230,19 @@ cudaError_t launch_group_admm_out(const GroupDesc* d, int count, float* z, cudaS
 // Device status bits.
 enum : int { STS_NONFINITE = 1, STS_TIMEOUT = 2, STS_BAD_ROW = 4, STS_DUP_ROW = 8 };
 
+// Batched instances whose n is 7-smooth but not a power of two (cs_smooth.cu):
+// mixed-radix FFTs, one persistent launch per solve.  smooth_plan takes the
+// batch's arrays and the `count` instances ids[] (rows and c as the batch
+// plan's; noff / moff their offsets); status is the batch's status word.
+struct SmoothSet;
+bool smooth_size(int64_t n);
+int smooth_plan(SmoothSet** out, const int* ids, int count, const int64_t* n, const int64_t* m,
+                const int64_t* noff, const int64_t* moff, const int64_t* rows, const double* c, int* status,
+                cudaStream_t s);
+cudaError_t smooth_ista(SmoothSet* q, const float* y, const float* lambda, const float* tau, int iters, float* x,
+                        cudaStream_t s);
+cudaError_t smooth_admm(SmoothSet* q, const float* y, const float* lambda, const float* rho, int iters, float* z,
+                        cudaStream_t s);
+void smooth_free(SmoothSet* q);
+
 }  // namespace csk

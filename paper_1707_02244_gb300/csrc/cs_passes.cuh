@@ -121,8 +121,21 @@ __device__ void block_accum(float v, double* dst, int blk) {
   }
 }
 
+// Complex element i (floats 2i, 2i + 1) of a float vector that may start at
+// any 4-byte boundary (a caller's slice of a concatenation of odd-length
+// vectors): one 8-byte access when the vector is 8-byte aligned, two 4-byte
+// ones otherwise; the test is the same for every thread of a launch.
 __device__ __forceinline__ float2 ld2(const float* p, int i) {
-  return __ldg(reinterpret_cast<const float2*>(p) + i);
+  if ((reinterpret_cast<uintptr_t>(p) & 7u) == 0) return __ldg(reinterpret_cast<const float2*>(p) + i);
+  return make_float2(__ldg(p + 2 * i), __ldg(p + 2 * i + 1));
+}
+__device__ __forceinline__ void st2(float* p, int i, float2 v) {
+  if ((reinterpret_cast<uintptr_t>(p) & 7u) == 0) {
+    reinterpret_cast<float2*>(p)[i] = v;
+  } else {
+    p[2 * i] = v.x;
+    p[2 * i + 1] = v.y;
+  }
 }
 
 // ---------------------------------------------------------------- epilogues
@@ -150,7 +163,7 @@ template <> struct Epi<COL_LOAD_SCALED> {
   __device__ static float2 apply(const KParams& kp, const CallArgs& a, float2, int p, int t, Acc&) {
     const float s = (float)rsqrt(kp.pp.stats[ST_X2]);
     float2 u = cscale(ld2(a.src, p), s);
-    reinterpret_cast<float2*>(a.aux)[p] = u;
+    st2(a.aux, p, u);
     return u;
   }
 };
@@ -158,7 +171,7 @@ template <> struct Epi<COL_LOAD_SCALED> {
 template <> struct Epi<COL_STORE> {
   static constexpr bool kRead = true, kFwd = false;
   __device__ static float2 apply(const KParams&, const CallArgs& a, float2 v, int p, int t, Acc&) {
-    reinterpret_cast<float2*>(a.dst)[p] = v;
+    st2(a.dst, p, v);
     return v;
   }
 };
@@ -224,7 +237,7 @@ template <> struct Epi<COL_POWER_OUT> {
   static constexpr bool kRead = true, kFwd = false;
   __device__ static float2 apply(const KParams&, const CallArgs& a, float2 w, int p, int t, Acc& acc) {
     const float2 u = ld2(a.aux, p);
-    reinterpret_cast<float2*>(a.dst)[p] = w;
+    st2(a.dst, p, w);
     acc.v[ST_X2] = fmaf(w.x, w.x, fmaf(w.y, w.y, acc.v[ST_X2]));
     acc.v[ST_DX2] = fmaf(u.x, w.x, fmaf(u.y, w.y, acc.v[ST_DX2]));
     return w;
@@ -368,7 +381,7 @@ template <> struct Epi<COL_RES_SAVE> {
     const float r0 = (mm & 1u) ? __ldg(kp.pp.ys + i0) - v.x : 0.f;
     const float r1 = (mm & 2u) ? __ldg(kp.pp.ys + i0 + (int)(mm & 1u)) - v.y : 0.f;
     const float2 r = make_float2(r0, r1);
-    reinterpret_cast<float2*>(a.v)[t] = r;
+    st2(a.v, t, r);
     return r;
   }
 };
@@ -378,7 +391,7 @@ template <> struct Epi<COL_ISTA_SEG> {
   __device__ static float2 apply(const KParams&, const CallArgs& a, float2 g, int p, int t, Acc&) {
     const float2 xo = ld2(a.x, t);
     const float2 xn = make_float2(soft(fmaf(a.tau, g.x, xo.x), a.thr), soft(fmaf(a.tau, g.y, xo.y), a.thr));
-    reinterpret_cast<float2*>(a.z)[t] = xn;
+    st2(a.z, t, xn);
     return xn;
   }
 };
@@ -390,7 +403,7 @@ template <> struct Epi<COL_GRAD_W> {
     const float2 g = ld2(a.dst, t), xn = ld2(a.z, t);
     const float2 w = make_float2(xn.x != 0.f ? g.x : 0.f, xn.y != 0.f ? g.y : 0.f);
     acc.v[0] -= sgnf(xn.x) * w.x + sgnf(xn.y) * w.y;
-    reinterpret_cast<float2*>(a.mu)[t] = w;
+    st2(a.mu, t, w);
     return w;
   }
 };
@@ -405,7 +418,7 @@ template <> struct Epi<COL_GRAD_MASK> {
     if (mm & 1u) a.aux[i0] = fmaf(a.tau, v.x, a.aux[i0]);
     if (mm & 2u) a.aux[i0 + (int)(mm & 1u)] = fmaf(a.tau, v.y, a.aux[i0 + (int)(mm & 1u)]);
     const float2 q = make_float2((mm & 1u) ? v.x : 0.f, (mm & 2u) ? v.y : 0.f);
-    reinterpret_cast<float2*>(a.nu)[t] = q;
+    st2(a.nu, t, q);
     return q;
   }
 };
@@ -415,7 +428,7 @@ template <> struct Epi<COL_GRAD_G> {
   __device__ static float2 apply(const KParams&, const CallArgs& a, float2 v, int p, int t, Acc&) {
     const float2 w = ld2(a.mu, t);
     const float2 g = make_float2(fmaf(-a.tau, v.x, w.x), fmaf(-a.tau, v.y, w.y));
-    reinterpret_cast<float2*>(a.dst)[t] = g;
+    st2(a.dst, t, g);
     return g;
   }
 };

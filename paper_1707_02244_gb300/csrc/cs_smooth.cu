@@ -1,0 +1,1219 @@
+// Batched solves of instances whose length n is 7-smooth (n = 2^a 3^b 5^c 7^d)
+// but not a power of two.
+//
+// Every FFT is a mixed-radix Stockham transform in shared memory (radices 8,
+// 4, 2, 7, 5, 3; ping-pong between two buffers, one barrier per stage).  An
+// instance with n <= SM_WHOLE_MAX is solved whole by one CTA; a larger one by
+// the four-step split n = N1 x N2 of a complex length-n FFT, the vector held
+// as an N2 x N1 row-major array in natural order (element j = N1 j2 + j1):
+//   column pass: length-N2 FFTs down G columns (j2 -> k2), the element-wise
+//                step of the solver between the inverse and the forward one;
+//   mid pass:    the twiddle w_n^(j1 k2), length-N1 FFTs along the rows
+//                (j1 -> k1, giving X[k2 + N2 k1] at (k2, k1)), the spectral
+//                operator, and the way back.
+// ISTA transforms its real vectors as complex ones (imaginary part zero);
+// ADMM packs (v + mu) + i (z - nu) as in the power-of-two solver and pairs
+// frequency k with n - k: (k2, k1) ~ (N2 - k2, N1 - 1 - k1) for k2 > 0,
+// (0, k1) ~ (0, (N1 - k1) mod N1).
+//
+// A whole solve is ONE persistent cooperative launch.  Its CTAs take work
+// items from a device-side queue (one 64-bit counter) in a fixed order:
+// first the whole-CTA instances (largest first), then pass by pass and
+// iteration by iteration the tiles of every large instance.  A tile waits
+// until its instance has completed every tile of the pass before (one
+// monotonic counter per instance, release/acquire through L2); every wait is
+// bounded and latches STS_TIMEOUT, after which all CTAs stop taking items.
+// Items are taken in queue order, so every item a tile can wait on was taken
+// earlier by a running CTA: the schedule cannot deadlock.
+//
+// The split N1 x N2 and the column-tile width G of every large n come from a
+// plan-time tuner (a few timed candidate solves on scratch buffers, cached
+// per n for the process; CS_BATCH_AUTOTUNE=0 keeps the heuristic choice).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/cs.h"
+#include "cs_fft.cuh"
+#include "cs_internal.h"
+
+namespace csk {
+
+constexpr int SM_NT = 256;             // threads per CTA
+constexpr int SM_TILE = 4096;          // complex values per shared buffer (two buffers)
+constexpr int SM_WHOLE_MAX = 4096;     // n solved whole by one CTA
+constexpr int64_t SM_N_MAX = int64_t(1) << 20;
+constexpr int SM_MAXST = 12;           // stages of one FFT (<= 8 for lengths <= 4096)
+constexpr unsigned long long SM_WAIT_NS = 2000000000ull;   // bounded wait on a counter: 2 s
+constexpr unsigned SM_SPIN_MAX = 1u << 24;
+
+struct SmInst {
+  int n, N1, N2, G;        // G = 0: whole-CTA instance (N1 = n, N2 = 1)
+  int ncol, nmid, R;       // tiles of a column / mid pass; rows of an ISTA mid tile
+  int s1, s2;              // stages of the length-N1 / length-N2 FFT
+  float inv_n;
+  int pad0;
+  int64_t noff;            // x / z in the caller's concatenated n-vectors
+  int64_t soff;            // y~, mu, nu and the spectrum tables (n entries each)
+  int64_t woff;            // exchange buffer (complex, n), large instances
+  int64_t twoff;           // tw1 (N1), tw2 (N2), T1 (N1)
+  unsigned char r1[SM_MAXST], r2[SM_MAXST];
+};
+
+struct SmScal {   // per call and instance
+  float thr, tau, rho, sigma, tau1, tau2, d_on, d_off;
+};
+
+struct SmRun {
+  const SmInst* inst;
+  const SmScal* sc;
+  const int* whole;            // whole-CTA instances, largest first
+  const int2* cmap;            // (instance, tile) of every column tile of the large instances
+  const int2* mmap;            // ... and of every mid tile
+  int n_whole, C, M;           // whole-CTA items; column / mid tiles per pass
+  int admm, iters;
+  long long items;
+  float2* W;
+  const float2* chat;          // spectrum c^ in matrix order (k2, k1) ~ X[k2 + N2 k1]
+  const float* bhat;           // 1 / (rho |c^|^2 + sigma), same order
+  const float2* tw;
+  const float* yt;             // P^T y with NaN off the sampled rows
+  float* x;                    // ISTA: x (in / out); ADMM: z (out)
+  float* mu;
+  float* nu;
+  unsigned long long* queue;
+  unsigned long long* done;    // per instance: tiles completed
+  int* status;
+};
+
+namespace {
+
+// ------------------------------------------------------------ device math
+
+__device__ __forceinline__ float soft_s(float u, float g) { return u > g ? u - g : (u < -g ? u + g : 0.f); }
+
+// cos / sin (2 pi m / R), m = 1 .. (R - 1) / 2, for the odd radices
+__device__ __forceinline__ float kc(int R, int m) {
+  if (R == 3) return -0.5f;
+  if (R == 5) return m == 1 ? 0.30901699437494745f : -0.8090169943749473f;
+  return m == 1 ? 0.6234898018587336f : (m == 2 ? -0.22252093395631434f : -0.900968867902419f);
+}
+__device__ __forceinline__ float ks(int R, int m) {
+  if (R == 3) return 0.8660254037844387f;
+  if (R == 5) return m == 1 ? 0.9510565162951535f : 0.5877852522924732f;
+  return m == 1 ? 0.7818314824680298f : (m == 2 ? 0.9749279121818236f : 0.43388373911755823f);
+}
+
+// y_k = sum_q v_q exp(DIR 2 pi i q k / R)   (DIR = -1 forward, +1 inverse)
+template <int DIR>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3);
+  const float2 d13 = mul_diri<DIR>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void dft(float2 (&v)[R]) {
+  if constexpr (R == 2) {
+    const float2 a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+  } else if constexpr (R == 4) {
+    dft4<DIR>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<DIR>(e0, e1, e2, e3);
+    dft4<DIR>(o0, o1, o2, o3);
+    const float h = 0.7071067811865476f;
+    // w = exp(DIR 2 pi i / 8) = h (1 + DIR i); w^2 = DIR i; w^3 = DIR i w
+    const float2 w1 = make_float2(h * (o1.x - DIR * o1.y), h * (o1.y + DIR * o1.x));
+    const float2 w2 = mul_diri<DIR>(o2);
+    const float2 t3 = make_float2(h * (o3.x - DIR * o3.y), h * (o3.y + DIR * o3.x));
+    const float2 w3 = mul_diri<DIR>(t3);
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, w1);
+    v[5] = csub(e1, w1);
+    v[2] = cadd(e2, w2);
+    v[6] = csub(e2, w2);
+    v[3] = cadd(e3, w3);
+    v[7] = csub(e3, w3);
+  } else {
+    // odd R: pairs q, R - q share cos and flip sin
+    constexpr int H = (R - 1) / 2;
+    float2 sp[H], sm[H];
+    float2 y0 = v[0];
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+      sp[q - 1] = cadd(v[q], v[R - q]);
+      sm[q - 1] = csub(v[q], v[R - q]);
+      y0 = cadd(y0, sp[q - 1]);
+    }
+    float2 out[R];
+    out[0] = y0;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+      float2 a = v[0], b = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 1; q <= H; ++q) {
+        const int m = (q * k) % R;
+        const float c = m <= H ? kc(R, m) : kc(R, R - m);
+        const float s = m <= H ? ks(R, m) : -ks(R, R - m);
+        a = make_float2(fmaf(c, sp[q - 1].x, a.x), fmaf(c, sp[q - 1].y, a.y));
+        b = make_float2(fmaf(s, sm[q - 1].x, b.x), fmaf(s, sm[q - 1].y, b.y));
+      }
+      const float2 ib = mul_diri<DIR>(b);
+      out[k] = cadd(a, ib);
+      out[R - k] = csub(a, ib);
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = out[q];
+  }
+}
+
+// One Stockham stage of radix R over F independent length-L FFTs, element e
+// of FFT f at f * fs + e * es.  Ns = product of the earlier radices; the
+// butterfly j reads e = j + q L/R and writes e = (j - k) R + k + q Ns,
+// k = j mod Ns, after the twiddles w_L^(k q L / (Ns R)).  `ffast`: the
+// thread index runs over f first (columns), else over j (rows).
+template <int R, int DIR>
+__device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int L, int F, int fs, int es,
+                                         bool ffast, int Ns, const float2* __restrict__ tw) {
+  const int B = L / R;
+  const int step = L / (Ns * R);
+  const int tot = B * F;
+  for (int idx = threadIdx.x; idx < tot; idx += SM_NT) {
+    int f, j;
+    if (ffast) {
+      j = idx / F;
+      f = idx - j * F;
+    } else {
+      f = idx / B;
+      j = idx - f * B;
+    }
+    const int base = f * fs;
+    const int k = j % Ns;
+    float2 v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = src[base + (j + q * B) * es];
+    if (k > 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        float2 w = __ldg(tw + k * q * step);
+        if (DIR > 0) w.y = -w.y;
+        v[q] = cmul(v[q], w);
+      }
+    }
+    dft<R, DIR>(v);
+    const int o = (j - k) * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) dst[base + (o + q * Ns) * es] = v[q];
+  }
+}
+
+// The whole transform; returns the buffer that holds the result.
+template <int DIR>
+__device__ float2* mr_fft(float2* a, float2* b, int L, int F, int fs, int es, bool ffast,
+                          const unsigned char* rad, int S, const float2* __restrict__ tw) {
+  int Ns = 1;
+  for (int s = 0; s < S; ++s) {
+    const int R = rad[s];
+    switch (R) {
+      case 8: mr_stage<8, DIR>(a, b, L, F, fs, es, ffast, Ns, tw); break;
+      case 4: mr_stage<4, DIR>(a, b, L, F, fs, es, ffast, Ns, tw); break;
+      case 2: mr_stage<2, DIR>(a, b, L, F, fs, es, ffast, Ns, tw); break;
+      case 7: mr_stage<7, DIR>(a, b, L, F, fs, es, ffast, Ns, tw); break;
+      case 5: mr_stage<5, DIR>(a, b, L, F, fs, es, ffast, Ns, tw); break;
+      default: mr_stage<3, DIR>(a, b, L, F, fs, es, ffast, Ns, tw); break;
+    }
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+// Algorithm 3's x-update on the pair (Z_k, Z_{n-k}) of the packed spectrum
+// of (v + mu) + i (z - nu): V, W untangled, X = b (rho c V + sigma W),
+// P = conj(c) X, written back as X + i P at k and its mirror at n - k.
+__device__ __forceinline__ void pair_admm(float2 ch, float bb, float rho, float sigma, float2& za, float2& zb) {
+  const float2 V = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+  const float2 Wk = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+  const float2 cv = cmul(ch, V);
+  const float2 X = make_float2(bb * fmaf(rho, cv.x, sigma * Wk.x), bb * fmaf(rho, cv.y, sigma * Wk.y));
+  const float2 Pc = cmulc(X, ch);
+  za = make_float2(X.x - Pc.y, X.y + Pc.x);
+  zb = make_float2(X.x + Pc.y, Pc.x - X.y);
+}
+
+// Row 0 (and the whole vector of a whole-CTA instance): k1 ~ (N1 - k1) mod N1.
+__device__ __forceinline__ void pairs_row0(float2* S, int N1, const float2* __restrict__ ch,
+                                           const float* __restrict__ bh, const SmScal& s) {
+  for (int k1 = threadIdx.x; k1 <= (N1 >> 1); k1 += SM_NT) {
+    const int kb = k1 == 0 ? 0 : N1 - k1;
+    float2 za = S[k1], zb = S[kb];
+    pair_admm(__ldg(ch + k1), __ldg(bh + k1), s.rho, s.sigma, za, zb);
+    S[kb] = zb;   // self-pairs keep the k-side value
+    S[k1] = za;
+  }
+  __syncthreads();
+}
+
+// Algorithm 3's element-wise steps at one element (see the power-of-two
+// column pass): returns the next packed input (v + mu) + i (z - nu).
+__device__ __forceinline__ float2 admm_elem(const SmRun& r, const SmInst& d, const SmScal& s, int64_t t, float x,
+                                            float cx, bool last) {
+  const float yv = __ldg(r.yt + d.soff + t);
+  const bool on = !isnan(yv);
+  const float mu = __ldcg(r.mu + d.soff + t), nu = __ldcg(r.nu + d.soff + t);
+  const float v = (on ? s.d_on : s.d_off) * fmaf(s.rho, cx - mu, on ? yv : 0.f);
+  const float z = soft_s(x + nu, s.thr);
+  const float mu2 = fmaf(s.tau1, v - cx, mu);
+  const float nu2 = fmaf(s.tau2, x - z, nu);
+  __stcg(r.mu + d.soff + t, mu2);
+  __stcg(r.nu + d.soff + t, nu2);
+  if (last) __stcg(r.x + d.noff + t, z);
+  return make_float2(v + mu2, z - nu2);
+}
+
+// ------------------------------------------------------- whole-CTA solve
+
+__device__ void whole_solve(const SmRun& r, const SmInst& d, const SmScal& s, float2* A, float2* B) {
+  const int n = d.n;
+  const float2* tw = r.tw + d.twoff;
+  const float2* ch = r.chat + d.soff;
+  if (!r.admm) {
+    for (int t = threadIdx.x; t < n; t += SM_NT) A[t] = make_float2(__ldcg(r.x + d.noff + t), 0.f);
+    __syncthreads();
+    for (int it = 0; it < r.iters; ++it) {
+      float2* u = mr_fft<-1>(A, B, n, 1, 0, 1, false, d.r1, d.s1, tw);
+      for (int k = threadIdx.x; k < n; k += SM_NT) u[k] = cmulc(u[k], __ldg(ch + k));
+      __syncthreads();
+      float2* o = u == A ? B : A;
+      u = mr_fft<+1>(u, o, n, 1, 0, 1, false, d.r1, d.s1, tw);
+      // r~ = M (y~ - C x)
+      for (int t = threadIdx.x; t < n; t += SM_NT) {
+        const float yv = __ldg(r.yt + d.soff + t);
+        u[t] = make_float2(isnan(yv) ? 0.f : yv - u[t].x * d.inv_n, 0.f);
+      }
+      __syncthreads();
+      o = u == A ? B : A;
+      u = mr_fft<-1>(u, o, n, 1, 0, 1, false, d.r1, d.s1, tw);
+      for (int k = threadIdx.x; k < n; k += SM_NT) u[k] = cmul(u[k], __ldg(ch + k));
+      __syncthreads();
+      o = u == A ? B : A;
+      u = mr_fft<+1>(u, o, n, 1, 0, 1, false, d.r1, d.s1, tw);
+      // x <- eta_{tau lambda}(x + tau C^T r~)
+      for (int t = threadIdx.x; t < n; t += SM_NT) {
+        const float xo = __ldcg(r.x + d.noff + t);
+        const float xn = soft_s(fmaf(s.tau, u[t].x * d.inv_n, xo), s.thr);
+        __stcg(r.x + d.noff + t, xn);
+        A[t] = make_float2(xn, 0.f);   // A is free again: the next forward input
+      }
+      __syncthreads();
+    }
+  } else {
+    const float* bh = r.bhat + d.soff;
+    for (int t = threadIdx.x; t < n; t += SM_NT) A[t] = make_float2(0.f, 0.f);   // zero start
+    __syncthreads();
+    for (int it = 0; it < r.iters; ++it) {
+      float2* u = mr_fft<-1>(A, B, n, 1, 0, 1, false, d.r1, d.s1, tw);
+      pairs_row0(u, n, ch, bh, s);
+      float2* o = u == A ? B : A;
+      u = mr_fft<+1>(u, o, n, 1, 0, 1, false, d.r1, d.s1, tw);
+      const bool last = it + 1 == r.iters;
+      for (int t = threadIdx.x; t < n; t += SM_NT) {
+        const float2 q = u[t];
+        A[t] = admm_elem(r, d, s, t, q.x * d.inv_n, q.y * d.inv_n, last);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ----------------------------------------------------- four-step tiles
+
+enum : int { CK_FWD = 0, CK_RES = 1, CK_UPD = 2, CK_ADMM = 3 };
+
+// Column tile u: columns [u G, u G + Gt) of all N2 rows.
+__device__ void col_tile(const SmRun& r, const SmInst& d, const SmScal& s, int kind, int u, bool last, float2* A,
+                         float2* B) {
+  const int N1 = d.N1, N2 = d.N2, c0 = u * d.G;
+  const int Gt = min(d.G, N1 - c0);
+  const int tot = Gt * N2;
+  float2* W = r.W + d.woff;
+  const float2* tw2 = r.tw + d.twoff + N1;
+  for (int e = threadIdx.x; e < tot; e += SM_NT) {
+    const int j2 = e / Gt, c = e - j2 * Gt;
+    const int64_t g = (int64_t)j2 * N1 + c0 + c;
+    A[e] = kind == CK_FWD ? make_float2(__ldcg(r.x + d.noff + g), 0.f) : __ldcg(W + g);
+  }
+  __syncthreads();
+  float2* u2 = A;
+  if (kind != CK_FWD) {
+    u2 = mr_fft<+1>(A, B, N2, Gt, 1, Gt, true, d.r2, d.s2, tw2);
+    for (int e = threadIdx.x; e < tot; e += SM_NT) {
+      const int j2 = e / Gt, c = e - j2 * Gt;
+      const int64_t t = (int64_t)j2 * N1 + c0 + c;
+      const float2 q = u2[e];
+      float2 o;
+      if (kind == CK_RES) {
+        const float yv = __ldg(r.yt + d.soff + t);
+        o = make_float2(isnan(yv) ? 0.f : yv - q.x, 0.f);
+      } else if (kind == CK_UPD) {
+        const float xn = soft_s(fmaf(s.tau, q.x, __ldcg(r.x + d.noff + t)), s.thr);
+        __stcg(r.x + d.noff + t, xn);
+        o = make_float2(xn, 0.f);
+      } else {
+        o = admm_elem(r, d, s, t, q.x, q.y, last);
+      }
+      u2[e] = o;
+    }
+    __syncthreads();
+    if (last) return;
+  }
+  float2* o = u2 == A ? B : A;
+  u2 = mr_fft<-1>(u2, o, N2, Gt, 1, Gt, true, d.r2, d.s2, tw2);
+  for (int e = threadIdx.x; e < tot; e += SM_NT) {
+    const int j2 = e / Gt, c = e - j2 * Gt;
+    __stcg(W + (int64_t)j2 * N1 + c0 + c, u2[e]);
+  }
+}
+
+// Mid tile u.  ISTA: rows [u R, u R + nr), op conj(c^) (forward) or c^
+// (adjoint).  ADMM: row 0, row N2/2 (N2 even) or the pair (u, N2 - u).
+__device__ void mid_tile(const SmRun& r, const SmInst& d, const SmScal& s, int kind, int u, float2* A, float2* B) {
+  const int N1 = d.N1, N2 = d.N2;
+  int k2a, k2b, nr;
+  if (kind == 2) {
+    k2a = u;
+    k2b = N2 - u;
+    nr = (u == 0 || 2 * u == N2) ? 1 : 2;
+  } else {
+    k2a = u * d.R;
+    k2b = 0;
+    nr = min(d.R, N2 - k2a);
+  }
+  float2* W = r.W + d.woff;
+  const float2* tw1 = r.tw + d.twoff;
+  const float2* tw2 = tw1 + N1;
+  const float2* T1 = tw2 + N2;
+  const int tot = nr * N1;
+  auto row_of = [&](int f) { return kind == 2 ? (f == 0 ? k2a : k2b) : k2a + f; };
+  // w_n^(j1 k2) = T1[q mod N1] tw2[q div N1], q = j1 k2 < n
+  auto fourstep = [&](int j1, int k2) {
+    const int q = j1 * k2;
+    const int qh = q / N1;
+    return cmul(__ldg(T1 + (q - qh * N1)), __ldg(tw2 + qh));
+  };
+  for (int e = threadIdx.x; e < tot; e += SM_NT) {
+    const int f = e / N1, j1 = e - f * N1;
+    const int k2 = row_of(f);
+    A[e] = cmul(__ldcg(W + (int64_t)k2 * N1 + j1), fourstep(j1, k2));
+  }
+  __syncthreads();
+  float2* u2 = mr_fft<-1>(A, B, N1, nr, N1, 1, false, d.r1, d.s1, tw1);
+  const float2* ch = r.chat + d.soff;
+  if (kind != 2) {
+    for (int e = threadIdx.x; e < tot; e += SM_NT) {
+      const int f = e / N1, k1 = e - f * N1;
+      const float2 c = __ldg(ch + (int64_t)(k2a + f) * N1 + k1);
+      u2[e] = kind == 1 ? cmul(u2[e], c) : cmulc(u2[e], c);
+    }
+    __syncthreads();
+  } else {
+    const float* bh = r.bhat + d.soff;
+    if (k2a == 0) {
+      pairs_row0(u2, N1, ch, bh, s);
+    } else {
+      const int64_t rowoff = (int64_t)k2a * N1;
+      const int cnt = nr == 2 ? N1 : (N1 + 1) >> 1;   // self row N2/2: k1 <= N1 - 1 - k1
+      for (int k1 = threadIdx.x; k1 < cnt; k1 += SM_NT) {
+        const int ea = k1, eb = (nr == 2 ? N1 : 0) + N1 - 1 - k1;
+        float2 za = u2[ea], zb = u2[eb];
+        pair_admm(__ldg(ch + rowoff + k1), __ldg(bh + rowoff + k1), s.rho, s.sigma, za, zb);
+        u2[eb] = zb;
+        u2[ea] = za;
+      }
+      __syncthreads();
+    }
+  }
+  float2* o = u2 == A ? B : A;
+  u2 = mr_fft<+1>(u2, o, N1, nr, N1, 1, false, d.r1, d.s1, tw1);
+  for (int e = threadIdx.x; e < tot; e += SM_NT) {
+    const int f = e / N1, j1 = e - f * N1;
+    const int k2 = row_of(f);
+    __stcg(W + (int64_t)k2 * N1 + j1, cscale(cmulc(u2[e], fourstep(j1, k2)), d.inv_n));
+  }
+}
+
+// --------------------------------------------------------- the queue
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_status(const int* p) { return *(const volatile int*)p; }
+
+// Bounded wait until *cnt >= need (thread 0 of the CTA).
+__device__ bool wait_count(const unsigned long long* cnt, unsigned long long need, int* status) {
+  if (ld_acquire_u64(cnt) >= need) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned spin = 0; spin < SM_SPIN_MAX; ++spin) {
+    __nanosleep(256);
+    if (ld_acquire_u64(cnt) >= need) return true;
+    if ((spin & 63u) == 63u) {
+      if (ld_status(status) & STS_TIMEOUT) return false;
+      if (global_ns() - t0 > SM_WAIT_NS) break;
+    }
+  }
+  atomicOr(status, STS_TIMEOUT);
+  return false;
+}
+
+__global__ void __launch_bounds__(SM_NT) smooth_solve_k(const SmRun r) {
+  extern __shared__ float2 sbuf[];
+  __shared__ SmInst sd;
+  __shared__ long long s_item;
+  __shared__ int s_ok;
+  float2* A = sbuf;
+  float2* B = sbuf + SM_TILE;
+  const long long C = r.C, M = r.M;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      long long it = -1;
+      if (!(ld_status(r.status) & STS_TIMEOUT)) it = (long long)atomicAdd(r.queue, 1ull);
+      s_item = it;
+    }
+    __syncthreads();
+    const long long item = s_item;
+    if (item < 0 || item >= r.items) return;
+    if (item < r.n_whole) {
+      const int j = r.whole[item];
+      if (threadIdx.x == 0) sd = r.inst[j];
+      __syncthreads();
+      whole_solve(r, sd, r.sc[j], A, B);
+      __syncthreads();
+      continue;
+    }
+    // phase item: decode (pass kind, iteration, tile) and the counter it needs
+    long long p = item - r.n_whole;
+    int kind, col, u, j;
+    bool last = false;
+    unsigned long long need;
+    if (!r.admm) {
+      if (p < C) {
+        col = 1;
+        kind = CK_FWD;
+        const int2 m = r.cmap[p];
+        j = m.x;
+        u = m.y;
+        need = 0;
+      } else {
+        p -= C;
+        const long long per = 2 * C + 2 * M;
+        const long long t = p / per;
+        long long q = p - t * per;
+        int ph;
+        if (q < M) ph = 0;
+        else if (q < M + C) { ph = 1; q -= M; }
+        else if (q < 2 * M + C) { ph = 2; q -= M + C; }
+        else { ph = 3; q -= 2 * M + C; }
+        col = ph & 1;
+        const int2 m = col ? r.cmap[q] : r.mmap[q];
+        j = m.x;
+        u = m.y;
+        kind = ph == 0 ? 0 : (ph == 1 ? CK_RES : (ph == 2 ? 1 : CK_UPD));
+        last = ph == 3 && t + 1 == r.iters;
+        const SmInst& di = r.inst[j];
+        const unsigned long long nc = (unsigned)di.ncol, nm = (unsigned)di.nmid;
+        const unsigned long long off = ph == 0 ? 0 : (ph == 1 ? nm : (ph == 2 ? nm + nc : 2 * nm + nc));
+        need = nc + (unsigned long long)t * (2 * nc + 2 * nm) + off;
+      }
+    } else {
+      const long long per = C + M;
+      const long long t = p / per;
+      long long q = p - t * per;
+      col = q >= M;
+      if (col) q -= M;
+      const int2 m = col ? r.cmap[q] : r.mmap[q];
+      j = m.x;
+      u = m.y;
+      kind = col ? CK_ADMM : 2;
+      last = col && t + 1 == r.iters;
+      const SmInst& di = r.inst[j];
+      const unsigned long long nc = (unsigned)di.ncol, nm = (unsigned)di.nmid;
+      need = (unsigned long long)t * (nc + nm) + (col ? nm : 0);
+    }
+    if (threadIdx.x == 0) {
+      sd = r.inst[j];
+      s_ok = wait_count(r.done + j, need, r.status);
+      __threadfence();
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const SmScal s = r.sc[j];
+    if (col) col_tile(r, sd, s, kind, u, last, A, B);
+    else mid_tile(r, sd, s, kind, u, A, B);
+    __syncthreads();   // every store of the tile issued
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(r.done + j, 1ull);
+    }
+  }
+}
+
+// ----------------------------------------------------------- plan time
+
+// One radix-R stage of the FP64 transform of c (global memory, ping-pong).
+__global__ void fft64_mr_stage_k(const double2* __restrict__ a, double2* __restrict__ b, int L, int R, int Ns) {
+  const int B = L / R;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B) return;
+  const int k = j % Ns;
+  double2 v[8];
+  for (int q = 0; q < R; ++q) {
+    double2 x = a[j + q * B];
+    if (k > 0) {
+      double sn, cs;
+      sincospi(-2.0 * (double)(k * q) / (double)(Ns * R), &sn, &cs);
+      x = make_double2(x.x * cs - x.y * sn, x.x * sn + x.y * cs);
+    }
+    v[q] = x;
+  }
+  const int o = (j - k) * R + k;
+  for (int s = 0; s < R; ++s) {
+    double2 y = make_double2(0.0, 0.0);
+    for (int q = 0; q < R; ++q) {
+      double sn, cs;
+      sincospi(-2.0 * (double)((q * s) % R) / (double)R, &sn, &cs);
+      y.x += v[q].x * cs - v[q].y * sn;
+      y.y += v[q].x * sn + v[q].y * cs;
+    }
+    b[o + s * Ns] = y;
+  }
+}
+
+__global__ void real_to_c64_k(const double* __restrict__ c, double2* __restrict__ a, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) a[t] = make_double2(c[t], 0.0);
+}
+
+// c^ into matrix order (k2, k1) ~ k = k2 + N2 k1, rounded once; |c^|^2 in FP64.
+__global__ void sm_tab_k(const double2* __restrict__ chat, int N1, int N2, float2* __restrict__ cm,
+                         double* __restrict__ abs2) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N1 * N2) return;
+  const int k2 = e / N1, k1 = e - k2 * N1;
+  const double2 v = chat[k2 + N2 * k1];
+  cm[e] = make_float2((float)v.x, (float)v.y);
+  abs2[e] = v.x * v.x + v.y * v.y;
+}
+
+// b^ = 1 / (rho |c^|^2 + sigma) in FP64, stored fp32; one CTA per instance.
+__global__ void sm_tab_b_k(const SmInst* __restrict__ inst, const double* __restrict__ abs2,
+                           const double* __restrict__ rho, const double* __restrict__ sigma, float* __restrict__ bh) {
+  const SmInst& d = inst[blockIdx.x];
+  const double r = rho[blockIdx.x], sg = sigma[blockIdx.x];
+  for (int e = threadIdx.x; e < d.n; e += blockDim.x) bh[d.soff + e] = (float)(1.0 / (r * abs2[d.soff + e] + sg));
+}
+
+__global__ void sm_fill_nan_k(float* __restrict__ v, int64_t count) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) v[t] = __int_as_float(0x7fc00000);
+}
+
+// y~[pos[i]] = y[src[i]] (the sampled rows of every instance); a non-finite
+// y latches STS_NONFINITE.
+__global__ void sm_scatter_k(const float* __restrict__ y, const int64_t* __restrict__ src,
+                             const int64_t* __restrict__ pos, int64_t count, float* __restrict__ yt, int* status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const float v = y[src[i]];
+  if (!isfinite(v)) atomicOr(status, STS_NONFINITE);
+  yt[pos[i]] = v;
+}
+
+__global__ void sm_zero_out_k(const SmInst* __restrict__ inst, float* __restrict__ z) {
+  const SmInst& d = inst[blockIdx.x];
+  for (int e = threadIdx.x; e < d.n; e += blockDim.x) z[d.noff + e] = 0.f;
+}
+
+inline unsigned nblk(int64_t c, int nt = 256) { return (unsigned)((c + nt - 1) / nt); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host
+
+bool smooth_size(int64_t n) {
+  if (n < 16 || n > SM_N_MAX) return false;
+  if ((n & (n - 1)) == 0) return false;   // powers of two take the radix-16 solvers
+  int64_t v = n;
+  for (int p : {2, 3, 5, 7})
+    while (v % p == 0) v /= p;
+  return v == 1;
+}
+
+namespace {
+
+// Radices of a length-L FFT: 8s, then one 4 or 2, then 7s, 5s, 3s.
+int radix_plan(int L, unsigned char* out) {
+  int S = 0, p2 = 0;
+  while (L % 2 == 0) {
+    L /= 2;
+    ++p2;
+  }
+  for (; p2 >= 3; p2 -= 3) out[S++] = 8;
+  if (p2 == 2) out[S++] = 4;
+  if (p2 == 1) out[S++] = 2;
+  for (int p : {7, 5, 3})
+    while (L % p == 0) {
+      L /= p;
+      out[S++] = (unsigned char)p;
+    }
+  return S;
+}
+
+struct Split {
+  int N1, N2, G;
+};
+
+// Feasible splits n = N1 N2 (16 <= N2, N2 <= SM_TILE, N1 <= SM_TILE / 2 so
+// that an ADMM row pair fits a buffer), best first by the heuristic: N1 a
+// multiple of 4 (32-byte column segments), then N1 close to 2 N2.
+std::vector<Split> split_candidates(int64_t n) {
+  std::vector<Split> c;
+  for (int64_t N1 = 2; N1 <= SM_TILE / 2; ++N1) {
+    if (n % N1) continue;
+    const int64_t N2 = n / N1;
+    if (N2 < 16 || N2 > SM_TILE) continue;
+    int G = (int)std::min<int64_t>(std::min<int64_t>(8, SM_TILE / N2), N1);
+    c.push_back({(int)N1, (int)N2, G});
+  }
+  std::stable_sort(c.begin(), c.end(), [](const Split& a, const Split& b) {
+    const int ma = a.N1 % 4 != 0, mb = b.N1 % 4 != 0;
+    if (ma != mb) return ma < mb;
+    const double da = std::fabs(std::log2((double)a.N1 / (2.0 * a.N2)));
+    const double db = std::fabs(std::log2((double)b.N1 / (2.0 * b.N2)));
+    return da < db;
+  });
+  return c;
+}
+
+void fill_geometry(SmInst& d, int64_t n, const Split* sp) {
+  d.n = (int)n;
+  d.inv_n = (float)(1.0 / (double)n);
+  if (!sp) {
+    d.N1 = (int)n;
+    d.N2 = 1;
+    d.G = 0;
+    d.ncol = 0;
+    d.nmid = 0;
+    d.R = 1;
+    d.s1 = radix_plan(d.N1, d.r1);
+    d.s2 = 0;
+    return;
+  }
+  d.N1 = sp->N1;
+  d.N2 = sp->N2;
+  d.G = sp->G;
+  d.ncol = (d.N1 + d.G - 1) / d.G;
+  d.R = std::max(1, SM_TILE / d.N1);
+  d.s1 = radix_plan(d.N1, d.r1);
+  d.s2 = radix_plan(d.N2, d.r2);
+  d.nmid = 0;   // per solver: set by tiles_for
+}
+
+int mid_tiles(const SmInst& d, bool admm) { return admm ? d.N2 / 2 + 1 : (d.N2 + d.R - 1) / d.R; }
+
+cudaError_t set_smem_attr() {
+  static cudaError_t e = cudaFuncSetAttribute(smooth_solve_k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(2 * SM_TILE * sizeof(float2)));
+  return e;
+}
+
+cudaError_t launch_solve(const SmRun& r, cudaStream_t s) {
+  if (r.items <= 0) return cudaSuccess;
+  cudaError_t e = set_smem_attr();
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per = 0;
+  const size_t smem = 2 * SM_TILE * sizeof(float2);
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, smooth_solve_k, SM_NT, smem)) != cudaSuccess) return e;
+  const long long grid = std::min<long long>(r.items, (long long)std::max(1, per) * sms);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(SM_NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, smooth_solve_k, r);
+}
+
+}  // namespace
+
+struct SmoothSet {
+  int count = 0;
+  std::vector<int> ids;               // batch instance of every member
+  std::vector<SmInst> h;
+  std::vector<int> whole;             // members solved by one CTA, largest first
+  std::vector<int> large;             // members solved by four-step tiles
+  SmInst* d_inst = nullptr;           // ISTA mid tiling (nmid by rows)
+  SmInst* d_inst_a = nullptr;         // ADMM mid tiling (row pairs)
+  int* d_whole = nullptr;
+  int2 *cmap = nullptr, *mmap_i = nullptr, *mmap_a = nullptr;
+  int C = 0, Mi = 0, Ma = 0;
+  SmScal* sc = nullptr;
+  float2* W = nullptr;
+  float2* chat = nullptr;
+  float* bhat = nullptr;
+  double* abs2 = nullptr;
+  float2* tw = nullptr;
+  float* yt = nullptr;
+  float *mu = nullptr, *nu = nullptr;
+  int64_t* ysrc = nullptr;
+  int64_t* ypos = nullptr;
+  int64_t mcount = 0, stot = 0, wtot = 0;
+  unsigned long long* cnt = nullptr;  // [0] queue, [1 ..] per member
+  double *drho = nullptr, *dsigma = nullptr;
+  std::vector<double> host_rho, host_sigma;
+  int* status = nullptr;              // the batch's
+};
+
+namespace {
+
+template <typename T>
+cudaError_t salloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+// Split of a large n: tuned once per process (a 2-iteration ISTA solve of a
+// scratch instance per candidate, best of 3), else the heuristic's first.
+std::mutex g_tune_mu;
+std::map<int64_t, Split> g_tuned;
+
+cudaError_t tune_split(int64_t n, cudaStream_t s, Split* out) {
+  const std::vector<Split> cand = split_candidates(n);
+  if (cand.empty()) return cudaErrorInvalidValue;
+  const char* env = std::getenv("CS_BATCH_AUTOTUNE");
+  if ((env && env[0] == '0') || cand.size() == 1) {
+    *out = cand[0];
+    return cudaSuccess;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(n);
+    if (it != g_tuned.end()) {
+      *out = it->second;
+      return cudaSuccess;
+    }
+  }
+  Split best = cand[0];
+  {
+    const size_t nc = std::min<size_t>(cand.size(), 4);
+    SmInst* di = nullptr;
+    SmScal* ds = nullptr;
+    int2 *cm = nullptr, *mm = nullptr;
+    float2 *W = nullptr, *ch = nullptr, *tw = nullptr;
+    float *bh = nullptr, *yt = nullptr, *x = nullptr;
+    unsigned long long* cnt = nullptr;
+    int* st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto ok = [&](cudaError_t r) {
+      if (e == cudaSuccess) e = r;
+      return e == cudaSuccess;
+    };
+    ok(salloc(&di, 1));
+    ok(salloc(&ds, 1));
+    ok(salloc(&cm, SM_TILE * 2));
+    ok(salloc(&mm, SM_TILE * 2));
+    ok(salloc(&W, n));
+    ok(salloc(&ch, n));
+    ok(salloc(&tw, 2 * SM_TILE + SM_TILE));
+    ok(salloc(&bh, n));
+    ok(salloc(&yt, n));
+    ok(salloc(&x, n));
+    ok(salloc(&cnt, 2));
+    ok(salloc(&st, 1));
+    ok(cudaEventCreate(&e0));
+    ok(cudaEventCreate(&e1));
+    if (e == cudaSuccess) {
+      ok(cudaMemsetAsync(W, 0, n * sizeof(float2), s));
+      ok(cudaMemsetAsync(ch, 0, n * sizeof(float2), s));
+      ok(cudaMemsetAsync(tw, 0, 3 * SM_TILE * sizeof(float2), s));
+      ok(cudaMemsetAsync(yt, 0, n * sizeof(float), s));
+      ok(cudaMemsetAsync(x, 0, n * sizeof(float), s));
+      ok(cudaMemsetAsync(st, 0, sizeof(int), s));
+      const SmScal hs = {0.f, 1.f, 1.f, 1.f, 1.f, 1.f, 0.5f, 1.f};
+      ok(cudaMemcpyAsync(ds, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+    }
+    float best_ms = 1e30f;
+    for (size_t k = 0; k < nc && e == cudaSuccess; ++k) {
+      SmInst d = {};
+      fill_geometry(d, n, &cand[k]);
+      d.nmid = mid_tiles(d, false);
+      d.noff = d.soff = d.woff = d.twoff = 0;
+      std::vector<int2> hc, hm;
+      for (int t = 0; t < d.ncol; ++t) hc.push_back(make_int2(0, t));
+      for (int t = 0; t < d.nmid; ++t) hm.push_back(make_int2(0, t));
+      ok(cudaMemcpyAsync(di, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+      ok(cudaMemcpyAsync(cm, hc.data(), hc.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+      ok(cudaMemcpyAsync(mm, hm.data(), hm.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+      SmRun r = {};
+      r.inst = di;
+      r.sc = ds;
+      r.cmap = cm;
+      r.mmap = mm;
+      r.C = d.ncol;
+      r.M = d.nmid;
+      r.admm = 0;
+      r.iters = 2;
+      r.items = (long long)r.C + 2LL * (2 * r.C + 2 * r.M);
+      r.W = W;
+      r.chat = ch;
+      r.bhat = bh;
+      r.tw = tw;
+      r.yt = yt;
+      r.x = x;
+      r.queue = cnt;
+      r.done = cnt + 1;
+      r.status = st;
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        ok(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s));
+        ok(cudaEventRecord(e0, s));
+        ok(launch_solve(r, s));
+        ok(cudaEventRecord(e1, s));
+        ok(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        ok(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) ms_min = std::min(ms_min, ms);   // the first run warms up
+      }
+      if (e == cudaSuccess && ms_min < best_ms) {
+        best_ms = ms_min;
+        best = cand[k];
+      }
+    }
+    int hst = 0;
+    if (e == cudaSuccess) ok(cudaMemcpy(&hst, st, sizeof(int), cudaMemcpyDeviceToHost));
+    void* bufs[] = {di, ds, cm, mm, W, ch, tw, bh, yt, x, cnt, st};
+    for (void* p : bufs)
+      if (p) cudaFree(p);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    if (hst & STS_TIMEOUT) return cudaErrorLaunchTimeout;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[n] = best;
+  *out = best;
+  return cudaSuccess;
+}
+
+// FP64 forward FFT of the real c (length n) on the device; *out holds c^.
+cudaError_t fft64_mr(const double* c, double2* a, double2* b, int n, double2** out, cudaStream_t s) {
+  real_to_c64_k<<<nblk(n), 256, 0, s>>>(c, a, n);
+  unsigned char rad[32];
+  const int S = radix_plan(n, rad);
+  int Ns = 1;
+  for (int k = 0; k < S; ++k) {
+    fft64_mr_stage_k<<<nblk(n / rad[k]), 256, 0, s>>>(a, b, n, rad[k], Ns);
+    std::swap(a, b);
+    Ns *= rad[k];
+  }
+  *out = a;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+void smooth_free(SmoothSet* q) {
+  if (!q) return;
+  void* bufs[] = {q->d_inst, q->d_inst_a, q->d_whole, q->cmap, q->mmap_i, q->mmap_a, q->sc, q->W,
+                  q->chat, q->bhat, q->abs2, q->tw, q->yt, q->mu, q->nu, q->ysrc, q->ypos, q->cnt,
+                  q->drho, q->dsigma};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  delete q;
+}
+
+int smooth_plan(SmoothSet** out, const int* idv, int count, const int64_t* n, const int64_t* m,
+                      const int64_t* noff, const int64_t* moff, const int64_t* rows, const double* c, int* status,
+                      cudaStream_t s) {
+  const std::vector<int> ids(idv, idv + count);
+  *out = nullptr;
+  SmoothSet* q = new (std::nothrow) SmoothSet();
+  if (!q) return CS_ERR_NOMEM;
+  auto fail = [&](cs_status e) {
+    smooth_free(q);
+    return e;
+  };
+  auto cst = [](cudaError_t e) {
+    return e == cudaSuccess ? CS_OK : (e == cudaErrorMemoryAllocation ? CS_ERR_NOMEM : CS_ERR_CUDA);
+  };
+#define CS_S_TRY(expr)                  \
+  do {                                  \
+    cs_status e_ = cst(expr);           \
+    if (e_ != CS_OK) return fail(e_);   \
+  } while (0)
+  q->count = (int)ids.size();
+  q->ids = ids;
+  q->status = status;
+  q->h.resize(q->count);
+  // rows: distinct and in range (checked on the host, where they are)
+  int64_t so = 0, wo = 0, to = 0, mc = 0;
+  for (int k = 0; k < q->count; ++k) {
+    const int i = ids[k];
+    std::vector<char> seen(n[i], 0);
+    for (int64_t r = 0; r < m[i]; ++r) {
+      const int64_t row = rows[moff[i] + r];
+      if (row < 0 || row >= n[i] || seen[row]) return fail(CS_ERR_ARG);
+      seen[row] = 1;
+    }
+  }
+  for (int k = 0; k < q->count; ++k) {
+    const int i = ids[k];
+    SmInst& d = q->h[k];
+    d = SmInst{};
+    if (n[i] <= SM_WHOLE_MAX) {
+      fill_geometry(d, n[i], nullptr);
+      q->whole.push_back(k);
+    } else {
+      Split sp;
+      CS_S_TRY(tune_split(n[i], s, &sp));
+      fill_geometry(d, n[i], &sp);
+      q->large.push_back(k);
+      d.woff = wo;
+      wo += n[i];
+    }
+    d.noff = noff[i];
+    d.soff = so;
+    d.twoff = to;
+    so += n[i];
+    to += 2 * (int64_t)d.N1 + d.N2;
+    mc += m[i];
+  }
+  q->stot = so;
+  q->wtot = wo;
+  q->mcount = mc;
+  std::stable_sort(q->whole.begin(), q->whole.end(), [&](int a, int b) { return q->h[a].n > q->h[b].n; });
+  // maps of the column and mid tiles, instance-major (an instance's tiles
+  // together, so its next pass can start while later instances finish)
+  std::vector<int2> hc, hmi, hma;
+  std::vector<SmInst> hi = q->h, ha = q->h;
+  for (int k : q->large) {
+    hi[k].nmid = mid_tiles(q->h[k], false);
+    ha[k].nmid = mid_tiles(q->h[k], true);
+    for (int t = 0; t < q->h[k].ncol; ++t) hc.push_back(make_int2(k, t));
+    for (int t = 0; t < hi[k].nmid; ++t) hmi.push_back(make_int2(k, t));
+    for (int t = 0; t < ha[k].nmid; ++t) hma.push_back(make_int2(k, t));
+  }
+  q->C = (int)hc.size();
+  q->Mi = (int)hmi.size();
+  q->Ma = (int)hma.size();
+  CS_S_TRY(salloc(&q->d_inst, q->count));
+  CS_S_TRY(salloc(&q->d_inst_a, q->count));
+  CS_S_TRY(salloc(&q->d_whole, q->whole.size()));
+  CS_S_TRY(salloc(&q->cmap, hc.size()));
+  CS_S_TRY(salloc(&q->mmap_i, hmi.size()));
+  CS_S_TRY(salloc(&q->mmap_a, hma.size()));
+  CS_S_TRY(salloc(&q->sc, q->count));
+  CS_S_TRY(salloc(&q->W, wo));
+  CS_S_TRY(salloc(&q->chat, so));
+  CS_S_TRY(salloc(&q->bhat, so));
+  CS_S_TRY(salloc(&q->abs2, so));
+  CS_S_TRY(salloc(&q->tw, to));
+  CS_S_TRY(salloc(&q->yt, so));
+  CS_S_TRY(salloc(&q->mu, so));
+  CS_S_TRY(salloc(&q->nu, so));
+  CS_S_TRY(salloc(&q->ysrc, mc));
+  CS_S_TRY(salloc(&q->ypos, mc));
+  CS_S_TRY(salloc(&q->cnt, q->count + 1));
+  CS_S_TRY(salloc(&q->drho, q->count));
+  CS_S_TRY(salloc(&q->dsigma, q->count));
+  CS_S_TRY(cudaMemcpyAsync(q->d_inst, hi.data(), q->count * sizeof(SmInst), cudaMemcpyHostToDevice, s));
+  CS_S_TRY(cudaMemcpyAsync(q->d_inst_a, ha.data(), q->count * sizeof(SmInst), cudaMemcpyHostToDevice, s));
+  if (!q->whole.empty())
+    CS_S_TRY(cudaMemcpyAsync(q->d_whole, q->whole.data(), q->whole.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (!hc.empty()) CS_S_TRY(cudaMemcpyAsync(q->cmap, hc.data(), hc.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  if (!hmi.empty())
+    CS_S_TRY(cudaMemcpyAsync(q->mmap_i, hmi.data(), hmi.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  if (!hma.empty())
+    CS_S_TRY(cudaMemcpyAsync(q->mmap_a, hma.data(), hma.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  // measurement positions: y[moff + r] -> y~[soff + rows[r]]
+  {
+    std::vector<int64_t> src(mc), pos(mc);
+    int64_t o = 0;
+    for (int k = 0; k < q->count; ++k) {
+      const int i = ids[k];
+      for (int64_t r = 0; r < m[i]; ++r, ++o) {
+        src[o] = moff[i] + r;
+        pos[o] = q->h[k].soff + rows[moff[i] + r];
+      }
+    }
+    CS_S_TRY(cudaMemcpyAsync(q->ysrc, src.data(), mc * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CS_S_TRY(cudaMemcpyAsync(q->ypos, pos.data(), mc * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CS_S_TRY(cudaStreamSynchronize(s));
+  }
+  sm_fill_nan_k<<<nblk(so), 256, 0, s>>>(q->yt, so);
+  CS_S_TRY(cudaGetLastError());
+  // spectra (FP64 on the device, rounded once) and twiddle tables
+  int64_t nmax = 0;
+  for (int k = 0; k < q->count; ++k) nmax = std::max<int64_t>(nmax, q->h[k].n);
+  double* dc = nullptr;
+  double2 *fa = nullptr, *fb = nullptr;
+  CS_S_TRY(salloc(&dc, nmax));
+  CS_S_TRY(salloc(&fa, nmax));
+  CS_S_TRY(salloc(&fb, nmax));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < q->count && e == cudaSuccess; ++k) {
+    const SmInst& d = q->h[k];
+    const int i = ids[k];
+    e = cudaMemcpyAsync(dc, c + noff[i], d.n * sizeof(double), cudaMemcpyHostToDevice, s);
+    double2* ch = nullptr;
+    if (e == cudaSuccess) e = fft64_mr(dc, fa, fb, d.n, &ch, s);
+    if (e == cudaSuccess) {
+      sm_tab_k<<<nblk(d.n), 256, 0, s>>>(ch, d.N1, d.N2, q->chat + d.soff, q->abs2 + d.soff);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_twiddle(q->tw + d.twoff, d.N1, d.N1, s);
+    if (e == cudaSuccess) e = launch_twiddle(q->tw + d.twoff + d.N1, d.N2, d.N2, s);
+    if (e == cudaSuccess) e = launch_twiddle(q->tw + d.twoff + d.N1 + d.N2, d.N1, d.n, s);
+    // the staging buffers are reused by the next instance
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  cudaFree(dc);
+  cudaFree(fa);
+  cudaFree(fb);
+  CS_S_TRY(e);
+  q->host_rho.assign(q->count, -1.0);
+  q->host_sigma.assign(q->count, -1.0);
+#undef CS_S_TRY
+  *out = q;
+  return CS_OK;
+}
+
+namespace {
+
+SmRun base_run(SmoothSet* q, bool admm, int iters, float* xz) {
+  SmRun r = {};
+  r.inst = admm ? q->d_inst_a : q->d_inst;
+  r.sc = q->sc;
+  r.whole = q->d_whole;
+  r.n_whole = (int)q->whole.size();
+  r.cmap = q->cmap;
+  r.mmap = admm ? q->mmap_a : q->mmap_i;
+  r.C = q->C;
+  r.M = admm ? q->Ma : q->Mi;
+  r.admm = admm;
+  r.iters = iters;
+  const long long C = r.C, M = r.M;
+  r.items = r.n_whole + (admm ? (long long)iters * (C + M) : (C > 0 ? C + (long long)iters * (2 * C + 2 * M) : 0));
+  r.W = q->W;
+  r.chat = q->chat;
+  r.bhat = q->bhat;
+  r.tw = q->tw;
+  r.yt = q->yt;
+  r.x = xz;
+  r.mu = q->mu;
+  r.nu = q->nu;
+  r.queue = q->cnt;
+  r.done = q->cnt + 1;
+  r.status = q->status;
+  return r;
+}
+
+}  // namespace
+
+cudaError_t smooth_ista(SmoothSet* q, const float* y, const float* lambda, const float* tau, int iters, float* x,
+                        cudaStream_t s) {
+  if (!q || q->count == 0 || iters == 0) return cudaSuccess;
+  std::vector<SmScal> h(q->count);
+  for (int k = 0; k < q->count; ++k) {
+    const int i = q->ids[k];
+    h[k] = SmScal{};
+    h[k].thr = (float)((double)tau[i] * (double)lambda[i]);
+    h[k].tau = tau[i];
+  }
+  cudaError_t e = cudaMemcpyAsync(q->sc, h.data(), q->count * sizeof(SmScal), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && q->mcount > 0) {
+    sm_scatter_k<<<nblk(q->mcount), 256, 0, s>>>(y, q->ysrc, q->ypos, q->mcount, q->yt, q->status);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(q->cnt, 0, (q->count + 1) * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = launch_solve(base_run(q, false, iters, x), s);
+  return e;
+}
+
+cudaError_t smooth_admm(SmoothSet* q, const float* y, const float* lambda, const float* rho, int iters, float* z,
+                        cudaStream_t s) {
+  if (!q || q->count == 0) return cudaSuccess;
+  if (iters == 0) {
+    sm_zero_out_k<<<q->count, 256, 0, s>>>(q->d_inst, z);
+    return cudaGetLastError();
+  }
+  bool changed = false;
+  std::vector<SmScal> h(q->count);
+  for (int k = 0; k < q->count; ++k) {
+    const int i = q->ids[k];
+    const double r = rho[i];
+    if (r != q->host_rho[k]) changed = true;
+    q->host_rho[k] = r;
+    q->host_sigma[k] = r;
+    h[k] = SmScal{};
+    h[k].thr = (float)((double)lambda[i] / r);
+    h[k].rho = (float)r;
+    h[k].sigma = (float)r;
+    h[k].tau1 = 1.f;
+    h[k].tau2 = 1.f;
+    h[k].d_on = (float)(1.0 / (1.0 + r));
+    h[k].d_off = (float)(1.0 / r);
+  }
+  cudaError_t e = cudaMemcpyAsync(q->sc, h.data(), q->count * sizeof(SmScal), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && changed) {
+    e = cudaMemcpyAsync(q->drho, q->host_rho.data(), q->count * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(q->dsigma, q->host_sigma.data(), q->count * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      sm_tab_b_k<<<q->count, 256, 0, s>>>(q->d_inst, q->abs2, q->drho, q->dsigma, q->bhat);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess && q->mcount > 0) {
+    sm_scatter_k<<<nblk(q->mcount), 256, 0, s>>>(y, q->ysrc, q->ypos, q->mcount, q->yt, q->status);
+    e = cudaGetLastError();
+  }
+  // zero start: W (the packed spectrum of (v + mu) + i (z - nu)), mu, nu
+  if (e == cudaSuccess && q->wtot > 0) e = cudaMemsetAsync(q->W, 0, q->wtot * sizeof(float2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(q->mu, 0, q->stot * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(q->nu, 0, q->stot * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(q->cnt, 0, (q->count + 1) * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = launch_solve(base_run(q, true, iters, z), s);
+  return e;
+}
+
+}  // namespace csk

@@ -95,13 +95,43 @@ def large_instance(seed: int = LARGE_SEED, n: int = 1 << 22) -> Instance:
 BATCH_SEED = 1707003
 
 
-def batch_sizes(count: int, lg_lo: float, lg_hi: float, seed: int) -> tuple[np.ndarray, np.ndarray]:
+def smooth_numbers(hi: int) -> np.ndarray:
+    """All 7-smooth integers 2^a 3^b 5^c 7^d <= hi, ascending."""
+    out = []
+    p2 = 1
+    while p2 <= hi:
+        p3 = p2
+        while p3 <= hi:
+            p5 = p3
+            while p5 <= hi:
+                p7 = p5
+                while p7 <= hi:
+                    out.append(p7)
+                    p7 *= 7
+                p5 *= 5
+            p3 *= 3
+        p2 *= 2
+    return np.array(sorted(out), dtype=np.int64)
+
+
+def batch_sizes(count: int, lg_lo: float, lg_hi: float, seed: int,
+                snap: str = "pow2") -> tuple[np.ndarray, np.ndarray]:
     """Sizes of a batch of independent instances: n log-uniform in
-    [2^lg_lo, 2^lg_hi], snapped to the nearest power of two (log2 rounded),
-    m/n uniform in [0.2, 0.5]."""
+    [2^lg_lo, 2^lg_hi], snapped to the nearest power of two (log2 rounded,
+    snap="pow2") or to the nearest 7-smooth integer (snap="smooth", the
+    smaller on a tie), m/n uniform in [0.2, 0.5]."""
     g = rng(seed)
-    lg = np.rint(g.uniform(lg_lo, lg_hi, size=count)).astype(np.int64)
-    n = np.left_shift(np.int64(1), lg)
+    u = g.uniform(lg_lo, lg_hi, size=count)
+    if snap == "pow2":
+        n = np.left_shift(np.int64(1), np.rint(u).astype(np.int64))
+    elif snap == "smooth":
+        target = np.exp2(u)
+        cand = smooth_numbers(int(np.ceil(2.0 ** lg_hi)) * 2)
+        j = np.clip(np.searchsorted(cand, target), 1, len(cand) - 1)
+        lo, hi = cand[j - 1], cand[j]
+        n = np.where(target - lo <= hi - target, lo, hi).astype(np.int64)
+    else:
+        raise ValueError(snap)
     m = np.maximum(1, np.rint(g.uniform(0.2, 0.5, size=count) * n)).astype(np.int64)
     return n, m
 

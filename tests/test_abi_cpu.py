@@ -99,7 +99,7 @@ def test_batch_plan_rejects_bad_arguments_without_device(cs):
     bad_m = np.array([8, 129], dtype=np.int64)
     assert cs.raw_call("cs_batch_plan", ctypes.byref(h), 2, n.ctypes.data, bad_m.ctypes.data,
                        rows.ctypes.data, c.ctypes.data, None) == cs.CS_ERR_ARG
-    for bad in (96, 32, 1 << 22, 1 << 23):
+    for bad in (88, 32, 12, 1 << 22, 1 << 23, 1200000):
         bn = np.array([64, bad], dtype=np.int64)
         assert cs.raw_call("cs_batch_plan", ctypes.byref(h), 2, bn.ctypes.data, m.ctypes.data,
                            rows.ctypes.data, c.ctypes.data, None) == cs.CS_ERR_UNSUPPORTED, bad

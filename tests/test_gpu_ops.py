@@ -160,3 +160,44 @@ def test_opnorm2(cs):
         plan.close()
     assert Lg <= L * (1 + 1e-5)
     assert Lg >= L * (1 - 2e-2), (Lg, L)
+
+
+def test_plan_vectors_at_odd_float_offsets(cs):
+    """The n-vectors of cs_forward / cs_adjoint / cs_ista must be 8-byte
+    aligned: one that starts 4 bytes past an 8-byte boundary is an argument
+    error reported before anything is launched.  The m-vectors (y, r) and
+    ADMM's z may start there and give the same bits as aligned ones (the
+    batch calls, whose concatenations put odd-length instances at such
+    offsets, are covered by test_gpu_batch_smooth)."""
+    torch, dev = torch_dev()
+    n, m = 1 << 12, 1 << 10
+    g = synth.rng(3100)
+    c = synth.gaussian_c(g, n, m)
+    rows = synth.draw_rows(g, n, m)
+    x = to_dev(g.standard_normal(n).astype(np.float32))
+    plan = cs.cs_plan(n, m, rows, c, torch.cuda.current_stream(dev))
+
+    def odd(k):
+        return torch.zeros(k + 1, dtype=torch.float32, device=dev)[1:]
+    try:
+        xo = odd(n)
+        assert xo.data_ptr() % 8 == 4
+        ya = torch.zeros(m, device=dev)
+        for call in (lambda: cs.cs_forward(plan, xo, ya), lambda: cs.cs_adjoint(plan, ya, xo),
+                     lambda: cs.cs_ista(plan, ya, 1e-3, 0.05, 5, xo)):
+            with pytest.raises(cs.CsError) as e:
+                call()
+            assert e.value.code == cs.CS_ERR_ARG
+        yo = odd(m)
+        cs.cs_forward(plan, x, ya)
+        cs.cs_forward(plan, x, yo)
+        ga, go = torch.zeros(n, device=dev), torch.zeros(n, device=dev)
+        cs.cs_adjoint(plan, ya, ga)
+        cs.cs_adjoint(plan, yo, go)
+        za, zo = torch.zeros(n, device=dev), odd(n)
+        cs.cs_admm(plan, ya, 1e-3, 1.0, 10, za)
+        cs.cs_admm(plan, yo, 1e-3, 1.0, 10, zo)
+        assert cs.cs_status_sync(plan) == cs.CS_OK
+        assert torch.equal(ya, yo) and torch.equal(ga, go) and torch.equal(za, zo)
+    finally:
+        plan.close()

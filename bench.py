@@ -17,7 +17,7 @@ spectrum, tables) and the power iteration are set-up, reported separately.
   python bench.py --workload grad [--steps K] [--warmup W]
   python bench.py --workload context
   python bench.py --workload deblur2d [--steps K] [--warmup W] [--iters T]
-  CS_GRAPHS=0 python bench.py --workload profile-iter|profile-passes|profile-batch|profile-2d|profile-grad
+  CS_GRAPHS=0 python bench.py --workload profile-iter|profile-passes|profile-batch|profile-smooth|profile-2d|profile-grad
 
 The profile-* workloads are short fixed launch sequences for ncu captures
 (nothing is timed; with CS_GRAPHS=0 every kernel is its own launch, so ncu's
@@ -27,6 +27,9 @@ The profile-* workloads are short fixed launch sequences for ncu captures
                   times back to back (L2 as inside a solve);
   profile-batch   128 instances (64 of n = 8192, 64 of 4096), 5 ISTA and 5
                   ADMM iterations in the single-CTA kernels;
+  profile-smooth  48 instances of 7-smooth n log-uniform in [2^15, 2^18], 5 ISTA
+                  and 5 ADMM iterations in the persistent mixed-radix kernel
+                  (no tuner solves);
   profile-2d      the 4096 x 4096 star field, 3 ISTA and 3 ADMM iterations;
   profile-grad    n = 2^20, m = n/4, 4 unrolled ISTA steps, checkpoints every 2.
 
@@ -79,7 +82,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-NMSE, roofline and CPU legs")
     ap.add_argument("--workload", default="n2e22",
                     choices=["n2e22", "batched", "grad", "context", "deblur2d",
-                             "profile-iter", "profile-passes", "profile-batch", "profile-2d", "profile-grad"])
+                             "profile-iter", "profile-passes", "profile-batch", "profile-smooth", "profile-2d", "profile-grad"])
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched workload")
     ap.add_argument("--sizes", default="smooth", choices=["smooth", "pow2"],
                     help="batched workload: n snapped to 7-smooth integers or to powers of two")
@@ -930,6 +933,19 @@ def run_profile(args):
                              stream)
         y = torch.from_numpy(np.random.default_rng(0).standard_normal(int(m.sum())).astype(np.float32)).to(dev)
         x = torch.zeros(int(n.sum()), dtype=torch.float32, device=dev)
+        z = torch.zeros_like(x)
+        cs.cs_batch_ista(b, y, 1e-3, 0.05, 5, x)
+        cs.cs_batch_admm(b, y, 1e-3, 1.0, 5, z)
+        assert cs.cs_batch_status_sync(b) == cs.CS_OK
+        b.close()
+    elif mode == "profile-smooth":
+        os.environ["CS_BATCH_AUTOTUNE"] = "0"   # no tuner solves in the launch sequence
+        n, m = synth.batch_sizes(48, 15, 18, synth.BATCH_SEED, snap="smooth")
+        insts = synth.batch_instances(n, m)
+        b = cs.cs_batch_plan(n, m, np.concatenate([i.rows for i in insts]), np.concatenate([i.c for i in insts]),
+                             stream)
+        y = torch.from_numpy(np.random.default_rng(0).standard_normal(int(np.sum(m))).astype(np.float32)).to(dev)
+        x = torch.zeros(int(np.sum(n)), dtype=torch.float32, device=dev)
         z = torch.zeros_like(x)
         cs.cs_batch_ista(b, y, 1e-3, 0.05, 5, x)
         cs.cs_batch_admm(b, y, 1e-3, 1.0, 5, z)

@@ -181,35 +181,72 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
   }
 }
 
+// Quotient of small non-negative integers by a run-time divisor through a
+// float reciprocal (exact for x < 2^24, x / d < 2^22): one correction step
+// fixes the at most one-off estimate.
+struct FDiv {
+  float r;
+  int d;
+};
+__device__ __forceinline__ FDiv fdiv_of(int d) { return FDiv{1.0f / (float)d, d}; }
+__device__ __forceinline__ int fdiv(int x, FDiv f) {
+  int q = __float2int_rz((float)x * f.r);
+  const int rem = x - q * f.d;
+  if (rem >= f.d) ++q;
+  else if (rem < 0) --q;
+  return q;
+}
+
+// Shared buffers use the padded index pad(e) = e + e / 16 (as the
+// power-of-two passes): the stride-R writes of the early stages would
+// otherwise fall on few banks.
+
 // One Stockham stage of radix R over F independent length-L FFTs, element e
 // of FFT f at f * fs + e * es.  Ns = product of the earlier radices; the
 // butterfly j reads e = j + q L/R and writes e = (j - k) R + k + q Ns,
 // k = j mod Ns, after the twiddles w_L^(k q L / (Ns R)).  `ffast`: the
 // thread index runs over f first (columns), else over j (rows).
+// Twiddles w_L^m = exp(-2 pi i m / L), m < L, from a two-level table in
+// shared memory: lo[m mod 64] * hi[m div 64] (both FP64-rounded table
+// values, one product apart from a correctly rounded twiddle).  The CTA's
+// table for its FFT length is loaded once per tile (twl_load) instead of
+// reading a per-instance table from global memory for every element.
+constexpr int TWL_LO = 64, TWL_HI = SM_TILE / TWL_LO + 1;
+__device__ __forceinline__ void twl_load(float2* twl, const float2* __restrict__ tw, int L) {
+  for (int i = threadIdx.x; i < TWL_LO + TWL_HI; i += SM_NT) {
+    const int m = i < TWL_LO ? i : (i - TWL_LO) * TWL_LO;
+    twl[i] = m < L ? __ldg(tw + m) : make_float2(1.f, 0.f);
+  }
+}
+__device__ __forceinline__ float2 twl_get(const float2* twl, int m) {
+  return cmul(twl[m & (TWL_LO - 1)], twl[TWL_LO + (m >> 6)]);
+}
+
 template <int R, int DIR>
 __device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int L, int F, int fs, int es,
-                                         bool ffast, int Ns, const float2* __restrict__ tw) {
+                                         bool ffast, int Ns, const float2* twl) {
   const int B = L / R;
   const int step = L / (Ns * R);
   const int tot = B * F;
+  const FDiv dF = fdiv_of(F), dB = fdiv_of(B), dNs = fdiv_of(Ns);
   for (int idx = threadIdx.x; idx < tot; idx += SM_NT) {
     int f, j;
     if (ffast) {
-      j = idx / F;
+      j = fdiv(idx, dF);
       f = idx - j * F;
     } else {
-      f = idx / B;
+      f = fdiv(idx, dB);
       j = idx - f * B;
     }
     const int base = f * fs;
-    const int k = j % Ns;
+    const int k = j - fdiv(j, dNs) * Ns;
     float2 v[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = src[base + (j + q * B) * es];
+    for (int q = 0; q < R; ++q) v[q] = src[pad(base + (j + q * B) * es)];
     if (k > 0) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
-        float2 w = __ldg(tw + k * q * step);
+        float2 w = twl_get(twl, k * q * step);
         if (DIR > 0) w.y = -w.y;
         v[q] = cmul(v[q], w);
       }
@@ -217,24 +254,24 @@ __device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int L, 
     dft<R, DIR>(v);
     const int o = (j - k) * R + k;
 #pragma unroll
-    for (int q = 0; q < R; ++q) dst[base + (o + q * Ns) * es] = v[q];
+    for (int q = 0; q < R; ++q) dst[pad(base + (o + q * Ns) * es)] = v[q];
   }
 }
 
 // The whole transform; returns the buffer that holds the result.
 template <int DIR>
 __device__ float2* mr_fft(float2* a, float2* b, int L, int F, int fs, int es, bool ffast,
-                          const unsigned char* rad, int S, const float2* __restrict__ tw) {
+                          const unsigned char* rad, int S, const float2* twl) {
   int Ns = 1;
   for (int s = 0; s < S; ++s) {
     const int R = rad[s];
     switch (R) {
-      case 8: mr_stage<8, DIR>(a, b, L, F, fs, es, ffast, Ns, tw); break;
-      case 4: mr_stage<4, DIR>(a, b, L, F, fs, es, ffast, Ns, tw); break;
-      case 2: mr_stage<2, DIR>(a, b, L, F, fs, es, ffast, Ns, tw); break;
-      case 7: mr_stage<7, DIR>(a, b, L, F, fs, es, ffast, Ns, tw); break;
-      case 5: mr_stage<5, DIR>(a, b, L, F, fs, es, ffast, Ns, tw); break;
-      default: mr_stage<3, DIR>(a, b, L, F, fs, es, ffast, Ns, tw); break;
+      case 8: mr_stage<8, DIR>(a, b, L, F, fs, es, ffast, Ns, twl); break;
+      case 4: mr_stage<4, DIR>(a, b, L, F, fs, es, ffast, Ns, twl); break;
+      case 2: mr_stage<2, DIR>(a, b, L, F, fs, es, ffast, Ns, twl); break;
+      case 7: mr_stage<7, DIR>(a, b, L, F, fs, es, ffast, Ns, twl); break;
+      case 5: mr_stage<5, DIR>(a, b, L, F, fs, es, ffast, Ns, twl); break;
+      default: mr_stage<3, DIR>(a, b, L, F, fs, es, ffast, Ns, twl); break;
     }
     __syncthreads();
     float2* t = a;
@@ -263,10 +300,10 @@ __device__ __forceinline__ void pairs_row0(float2* S, int N1, const float2* __re
                                            const float* __restrict__ bh, const SmScal& s) {
   for (int k1 = threadIdx.x; k1 <= (N1 >> 1); k1 += SM_NT) {
     const int kb = k1 == 0 ? 0 : N1 - k1;
-    float2 za = S[k1], zb = S[kb];
+    float2 za = S[pad(k1)], zb = S[pad(kb)];
     pair_admm(__ldg(ch + k1), __ldg(bh + k1), s.rho, s.sigma, za, zb);
-    S[kb] = zb;   // self-pairs keep the k-side value
-    S[k1] = za;
+    S[pad(kb)] = zb;   // self-pairs keep the k-side value
+    S[pad(k1)] = za;
   }
   __syncthreads();
 }
@@ -290,53 +327,54 @@ __device__ __forceinline__ float2 admm_elem(const SmRun& r, const SmInst& d, con
 
 // ------------------------------------------------------- whole-CTA solve
 
-__device__ void whole_solve(const SmRun& r, const SmInst& d, const SmScal& s, float2* A, float2* B) {
+__device__ void whole_solve(const SmRun& r, const SmInst& d, const SmScal& s, float2* A, float2* B,
+                            float2* twl) {
   const int n = d.n;
-  const float2* tw = r.tw + d.twoff;
+  twl_load(twl, r.tw + d.twoff, n);   // read after the barrier that follows the first fill of A
   const float2* ch = r.chat + d.soff;
   if (!r.admm) {
-    for (int t = threadIdx.x; t < n; t += SM_NT) A[t] = make_float2(__ldcg(r.x + d.noff + t), 0.f);
+    for (int t = threadIdx.x; t < n; t += SM_NT) A[pad(t)] = make_float2(__ldcg(r.x + d.noff + t), 0.f);
     __syncthreads();
     for (int it = 0; it < r.iters; ++it) {
-      float2* u = mr_fft<-1>(A, B, n, 1, 0, 1, false, d.r1, d.s1, tw);
-      for (int k = threadIdx.x; k < n; k += SM_NT) u[k] = cmulc(u[k], __ldg(ch + k));
+      float2* u = mr_fft<-1>(A, B, n, 1, 0, 1, false, d.r1, d.s1, twl);
+      for (int k = threadIdx.x; k < n; k += SM_NT) u[pad(k)] = cmulc(u[pad(k)], __ldg(ch + k));
       __syncthreads();
       float2* o = u == A ? B : A;
-      u = mr_fft<+1>(u, o, n, 1, 0, 1, false, d.r1, d.s1, tw);
+      u = mr_fft<+1>(u, o, n, 1, 0, 1, false, d.r1, d.s1, twl);
       // r~ = M (y~ - C x)
       for (int t = threadIdx.x; t < n; t += SM_NT) {
         const float yv = __ldg(r.yt + d.soff + t);
-        u[t] = make_float2(isnan(yv) ? 0.f : yv - u[t].x * d.inv_n, 0.f);
+        u[pad(t)] = make_float2(isnan(yv) ? 0.f : yv - u[pad(t)].x * d.inv_n, 0.f);
       }
       __syncthreads();
       o = u == A ? B : A;
-      u = mr_fft<-1>(u, o, n, 1, 0, 1, false, d.r1, d.s1, tw);
-      for (int k = threadIdx.x; k < n; k += SM_NT) u[k] = cmul(u[k], __ldg(ch + k));
+      u = mr_fft<-1>(u, o, n, 1, 0, 1, false, d.r1, d.s1, twl);
+      for (int k = threadIdx.x; k < n; k += SM_NT) u[pad(k)] = cmul(u[pad(k)], __ldg(ch + k));
       __syncthreads();
       o = u == A ? B : A;
-      u = mr_fft<+1>(u, o, n, 1, 0, 1, false, d.r1, d.s1, tw);
+      u = mr_fft<+1>(u, o, n, 1, 0, 1, false, d.r1, d.s1, twl);
       // x <- eta_{tau lambda}(x + tau C^T r~)
       for (int t = threadIdx.x; t < n; t += SM_NT) {
         const float xo = __ldcg(r.x + d.noff + t);
-        const float xn = soft_s(fmaf(s.tau, u[t].x * d.inv_n, xo), s.thr);
+        const float xn = soft_s(fmaf(s.tau, u[pad(t)].x * d.inv_n, xo), s.thr);
         __stcg(r.x + d.noff + t, xn);
-        A[t] = make_float2(xn, 0.f);   // A is free again: the next forward input
+        A[pad(t)] = make_float2(xn, 0.f);   // A is free again: the next forward input
       }
       __syncthreads();
     }
   } else {
     const float* bh = r.bhat + d.soff;
-    for (int t = threadIdx.x; t < n; t += SM_NT) A[t] = make_float2(0.f, 0.f);   // zero start
+    for (int t = threadIdx.x; t < n; t += SM_NT) A[pad(t)] = make_float2(0.f, 0.f);   // zero start
     __syncthreads();
     for (int it = 0; it < r.iters; ++it) {
-      float2* u = mr_fft<-1>(A, B, n, 1, 0, 1, false, d.r1, d.s1, tw);
+      float2* u = mr_fft<-1>(A, B, n, 1, 0, 1, false, d.r1, d.s1, twl);
       pairs_row0(u, n, ch, bh, s);
       float2* o = u == A ? B : A;
-      u = mr_fft<+1>(u, o, n, 1, 0, 1, false, d.r1, d.s1, tw);
+      u = mr_fft<+1>(u, o, n, 1, 0, 1, false, d.r1, d.s1, twl);
       const bool last = it + 1 == r.iters;
       for (int t = threadIdx.x; t < n; t += SM_NT) {
-        const float2 q = u[t];
-        A[t] = admm_elem(r, d, s, t, q.x * d.inv_n, q.y * d.inv_n, last);
+        const float2 q = u[pad(t)];
+        A[pad(t)] = admm_elem(r, d, s, t, q.x * d.inv_n, q.y * d.inv_n, last);
       }
       __syncthreads();
     }
@@ -349,25 +387,26 @@ enum : int { CK_FWD = 0, CK_RES = 1, CK_UPD = 2, CK_ADMM = 3 };
 
 // Column tile u: columns [u G, u G + Gt) of all N2 rows.
 __device__ void col_tile(const SmRun& r, const SmInst& d, const SmScal& s, int kind, int u, bool last, float2* A,
-                         float2* B) {
+                         float2* B, float2* twl) {
   const int N1 = d.N1, N2 = d.N2, c0 = u * d.G;
   const int Gt = min(d.G, N1 - c0);
   const int tot = Gt * N2;
   float2* W = r.W + d.woff;
-  const float2* tw2 = r.tw + d.twoff + N1;
+  twl_load(twl, r.tw + d.twoff + N1, N2);   // read after the barrier below
+  const FDiv dG = fdiv_of(Gt);
   for (int e = threadIdx.x; e < tot; e += SM_NT) {
-    const int j2 = e / Gt, c = e - j2 * Gt;
+    const int j2 = fdiv(e, dG), c = e - j2 * Gt;
     const int64_t g = (int64_t)j2 * N1 + c0 + c;
-    A[e] = kind == CK_FWD ? make_float2(__ldcg(r.x + d.noff + g), 0.f) : __ldcg(W + g);
+    A[pad(e)] = kind == CK_FWD ? make_float2(__ldcg(r.x + d.noff + g), 0.f) : __ldcg(W + g);
   }
   __syncthreads();
   float2* u2 = A;
   if (kind != CK_FWD) {
-    u2 = mr_fft<+1>(A, B, N2, Gt, 1, Gt, true, d.r2, d.s2, tw2);
+    u2 = mr_fft<+1>(A, B, N2, Gt, 1, Gt, true, d.r2, d.s2, twl);
     for (int e = threadIdx.x; e < tot; e += SM_NT) {
-      const int j2 = e / Gt, c = e - j2 * Gt;
+      const int j2 = fdiv(e, dG), c = e - j2 * Gt;
       const int64_t t = (int64_t)j2 * N1 + c0 + c;
-      const float2 q = u2[e];
+      const float2 q = u2[pad(e)];
       float2 o;
       if (kind == CK_RES) {
         const float yv = __ldg(r.yt + d.soff + t);
@@ -379,22 +418,23 @@ __device__ void col_tile(const SmRun& r, const SmInst& d, const SmScal& s, int k
       } else {
         o = admm_elem(r, d, s, t, q.x, q.y, last);
       }
-      u2[e] = o;
+      u2[pad(e)] = o;
     }
     __syncthreads();
     if (last) return;
   }
   float2* o = u2 == A ? B : A;
-  u2 = mr_fft<-1>(u2, o, N2, Gt, 1, Gt, true, d.r2, d.s2, tw2);
+  u2 = mr_fft<-1>(u2, o, N2, Gt, 1, Gt, true, d.r2, d.s2, twl);
   for (int e = threadIdx.x; e < tot; e += SM_NT) {
-    const int j2 = e / Gt, c = e - j2 * Gt;
-    __stcg(W + (int64_t)j2 * N1 + c0 + c, u2[e]);
+    const int j2 = fdiv(e, dG), c = e - j2 * Gt;
+    __stcg(W + (int64_t)j2 * N1 + c0 + c, u2[pad(e)]);
   }
 }
 
 // Mid tile u.  ISTA: rows [u R, u R + nr), op conj(c^) (forward) or c^
 // (adjoint).  ADMM: row 0, row N2/2 (N2 even) or the pair (u, N2 - u).
-__device__ void mid_tile(const SmRun& r, const SmInst& d, const SmScal& s, int kind, int u, float2* A, float2* B) {
+__device__ void mid_tile(const SmRun& r, const SmInst& d, const SmScal& s, int kind, int u, float2* A, float2* B,
+                         float2* twl, float2* tw4) {
   const int N1 = d.N1, N2 = d.N2;
   int k2a, k2b, nr;
   if (kind == 2) {
@@ -409,28 +449,33 @@ __device__ void mid_tile(const SmRun& r, const SmInst& d, const SmScal& s, int k
   float2* W = r.W + d.woff;
   const float2* tw1 = r.tw + d.twoff;
   const float2* tw2 = tw1 + N1;
-  const float2* T1 = tw2 + N2;
+  twl_load(twl, tw1, N1);   // read after the barrier below
+  // the four-step twiddle's two factors, each as a two-level table as well
+  twl_load(tw4, tw2 + N2, N1);
+  twl_load(tw4 + TWL_LO + TWL_HI, tw2, N2);
+  __syncthreads();
   const int tot = nr * N1;
   auto row_of = [&](int f) { return kind == 2 ? (f == 0 ? k2a : k2b) : k2a + f; };
   // w_n^(j1 k2) = T1[q mod N1] tw2[q div N1], q = j1 k2 < n
+  const FDiv dN1 = fdiv_of(N1);
   auto fourstep = [&](int j1, int k2) {
     const int q = j1 * k2;
-    const int qh = q / N1;
-    return cmul(__ldg(T1 + (q - qh * N1)), __ldg(tw2 + qh));
+    const int qh = fdiv(q, dN1);
+    return cmul(twl_get(tw4, q - qh * N1), twl_get(tw4 + TWL_LO + TWL_HI, qh));
   };
   for (int e = threadIdx.x; e < tot; e += SM_NT) {
-    const int f = e / N1, j1 = e - f * N1;
+    const int f = fdiv(e, dN1), j1 = e - f * N1;
     const int k2 = row_of(f);
-    A[e] = cmul(__ldcg(W + (int64_t)k2 * N1 + j1), fourstep(j1, k2));
+    A[pad(e)] = cmul(__ldcg(W + (int64_t)k2 * N1 + j1), fourstep(j1, k2));
   }
   __syncthreads();
-  float2* u2 = mr_fft<-1>(A, B, N1, nr, N1, 1, false, d.r1, d.s1, tw1);
+  float2* u2 = mr_fft<-1>(A, B, N1, nr, N1, 1, false, d.r1, d.s1, twl);
   const float2* ch = r.chat + d.soff;
   if (kind != 2) {
     for (int e = threadIdx.x; e < tot; e += SM_NT) {
-      const int f = e / N1, k1 = e - f * N1;
+      const int f = fdiv(e, dN1), k1 = e - f * N1;
       const float2 c = __ldg(ch + (int64_t)(k2a + f) * N1 + k1);
-      u2[e] = kind == 1 ? cmul(u2[e], c) : cmulc(u2[e], c);
+      u2[pad(e)] = kind == 1 ? cmul(u2[pad(e)], c) : cmulc(u2[pad(e)], c);
     }
     __syncthreads();
   } else {
@@ -442,20 +487,20 @@ __device__ void mid_tile(const SmRun& r, const SmInst& d, const SmScal& s, int k
       const int cnt = nr == 2 ? N1 : (N1 + 1) >> 1;   // self row N2/2: k1 <= N1 - 1 - k1
       for (int k1 = threadIdx.x; k1 < cnt; k1 += SM_NT) {
         const int ea = k1, eb = (nr == 2 ? N1 : 0) + N1 - 1 - k1;
-        float2 za = u2[ea], zb = u2[eb];
+        float2 za = u2[pad(ea)], zb = u2[pad(eb)];
         pair_admm(__ldg(ch + rowoff + k1), __ldg(bh + rowoff + k1), s.rho, s.sigma, za, zb);
-        u2[eb] = zb;
-        u2[ea] = za;
+        u2[pad(eb)] = zb;
+        u2[pad(ea)] = za;
       }
       __syncthreads();
     }
   }
   float2* o = u2 == A ? B : A;
-  u2 = mr_fft<+1>(u2, o, N1, nr, N1, 1, false, d.r1, d.s1, tw1);
+  u2 = mr_fft<+1>(u2, o, N1, nr, N1, 1, false, d.r1, d.s1, twl);
   for (int e = threadIdx.x; e < tot; e += SM_NT) {
-    const int f = e / N1, j1 = e - f * N1;
+    const int f = fdiv(e, dN1), j1 = e - f * N1;
     const int k2 = row_of(f);
-    __stcg(W + (int64_t)k2 * N1 + j1, cscale(cmulc(u2[e], fourstep(j1, k2)), d.inv_n));
+    __stcg(W + (int64_t)k2 * N1 + j1, cscale(cmulc(u2[pad(e)], fourstep(j1, k2)), d.inv_n));
   }
 }
 
@@ -489,13 +534,15 @@ __device__ bool wait_count(const unsigned long long* cnt, unsigned long long nee
   return false;
 }
 
-__global__ void __launch_bounds__(SM_NT) smooth_solve_k(const SmRun r) {
+__global__ void __launch_bounds__(SM_NT, 3) smooth_solve_k(const SmRun r) {
   extern __shared__ float2 sbuf[];
   __shared__ SmInst sd;
+  __shared__ float2 s_twl[TWL_LO + TWL_HI];
+  __shared__ float2 s_tw4[2 * (TWL_LO + TWL_HI)];
   __shared__ long long s_item;
   __shared__ int s_ok;
   float2* A = sbuf;
-  float2* B = sbuf + SM_TILE;
+  float2* B = sbuf + smem_slots(SM_TILE);
   const long long C = r.C, M = r.M;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -510,7 +557,7 @@ __global__ void __launch_bounds__(SM_NT) smooth_solve_k(const SmRun r) {
       const int j = r.whole[item];
       if (threadIdx.x == 0) sd = r.inst[j];
       __syncthreads();
-      whole_solve(r, sd, r.sc[j], A, B);
+      whole_solve(r, sd, r.sc[j], A, B, s_twl);
       __syncthreads();
       continue;
     }
@@ -571,8 +618,8 @@ __global__ void __launch_bounds__(SM_NT) smooth_solve_k(const SmRun r) {
     __syncthreads();
     if (!s_ok) return;
     const SmScal s = r.sc[j];
-    if (col) col_tile(r, sd, s, kind, u, last, A, B);
-    else mid_tile(r, sd, s, kind, u, A, B);
+    if (col) col_tile(r, sd, s, kind, u, last, A, B, s_twl);
+    else mid_tile(r, sd, s, kind, u, A, B, s_twl, s_tw4);
     __syncthreads();   // every store of the tile issued
     if (threadIdx.x == 0) {
       __threadfence();
@@ -746,7 +793,7 @@ int mid_tiles(const SmInst& d, bool admm) { return admm ? d.N2 / 2 + 1 : (d.N2 +
 
 cudaError_t set_smem_attr() {
   static cudaError_t e = cudaFuncSetAttribute(smooth_solve_k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)(2 * SM_TILE * sizeof(float2)));
+                                              (int)(2 * smem_slots(SM_TILE) * sizeof(float2)));
   return e;
 }
 
@@ -755,7 +802,7 @@ cudaError_t launch_solve(const SmRun& r, cudaStream_t s) {
   cudaError_t e = set_smem_attr();
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per = 0;
-  const size_t smem = 2 * SM_TILE * sizeof(float2);
+  const size_t smem = 2 * smem_slots(SM_TILE) * sizeof(float2);
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, smooth_solve_k, SM_NT, smem)) != cudaSuccess) return e;

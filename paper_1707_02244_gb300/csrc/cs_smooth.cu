@@ -90,6 +90,7 @@ struct SmRun {
   unsigned long long* queue;
   unsigned long long* done;    // per instance: tiles completed
   int* status;
+  unsigned long long stall;    // test hook: added to every count instance 0 waits for (0: off)
 };
 
 namespace {
@@ -610,6 +611,7 @@ __global__ void __launch_bounds__(SM_NT, 3) smooth_solve_k(const SmRun r) {
       const unsigned long long nc = (unsigned)di.ncol, nm = (unsigned)di.nmid;
       need = (unsigned long long)t * (nc + nm) + (col ? nm : 0);
     }
+    if (r.stall != 0ull && j == 0) need += r.stall;   // a count that is never reached
     if (threadIdx.x == 0) {
       sd = r.inst[j];
       s_ok = wait_count(r.done + j, need, r.status);
@@ -1194,6 +1196,17 @@ SmRun base_run(SmoothSet* q, bool admm, int iters, float* xz) {
   return r;
 }
 
+// Fault-injection hook for the bounded waits (tests only): with
+// CS_BATCH_STALL_TEST=k in the environment, every count that instance 0's
+// tiles wait for is raised by k, so the first such wait runs out (after
+// SM_WAIT_NS), latches STS_TIMEOUT and the whole launch returns; the host
+// then sees CS_ERR_TIMEOUT.  Nothing is armed when the variable is unset.
+SmRun with_stall(SmRun r) {
+  const char* env = std::getenv("CS_BATCH_STALL_TEST");
+  r.stall = env ? std::strtoull(env, nullptr, 10) : 0ull;
+  return r;
+}
+
 }  // namespace
 
 cudaError_t smooth_ista(SmoothSet* q, const float* y, const float* lambda, const float* tau, int iters, float* x,
@@ -1212,7 +1225,7 @@ cudaError_t smooth_ista(SmoothSet* q, const float* y, const float* lambda, const
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(q->cnt, 0, (q->count + 1) * sizeof(unsigned long long), s);
-  if (e == cudaSuccess) e = launch_solve(base_run(q, false, iters, x), s);
+  if (e == cudaSuccess) e = launch_solve(with_stall(base_run(q, false, iters, x)), s);
   return e;
 }
 
@@ -1259,7 +1272,7 @@ cudaError_t smooth_admm(SmoothSet* q, const float* y, const float* lambda, const
   if (e == cudaSuccess) e = cudaMemsetAsync(q->mu, 0, q->stot * sizeof(float), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(q->nu, 0, q->stot * sizeof(float), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(q->cnt, 0, (q->count + 1) * sizeof(unsigned long long), s);
-  if (e == cudaSuccess) e = launch_solve(base_run(q, true, iters, z), s);
+  if (e == cudaSuccess) e = launch_solve(with_stall(base_run(q, true, iters, z)), s);
   return e;
 }
 

@@ -183,3 +183,36 @@ def test_smooth_batch_nonfinite_measurement_is_reported(cs):
         assert cs.cs_batch_status_sync(b) == cs.CS_OK
     finally:
         b.close()
+
+
+def test_smooth_batch_bounded_wait_times_out(cs):
+    """Every device-side wait of the persistent launch is bounded.  The test
+    arms, from the host, a count that instance 0's tiles wait for and that no
+    tile ever reaches (CS_BATCH_STALL_TEST): the wait gives up after its
+    limit, latches the timeout, every CTA stops taking work and the launch
+    returns; the host reads CS_ERR_TIMEOUT.  The same batch then solves
+    normally, matching the oracle."""
+    import time
+    n, m, insts, ys, lam, tau, _ = _data([5000, 1000], 7700)
+    b = _plan(cs, n, m, insts)
+    torch, dev = torch_dev()
+    try:
+        x = torch.zeros(int(n.sum()), dtype=torch.float32, device=dev)
+        y = to_dev(np.concatenate(ys))
+        os.environ["CS_BATCH_STALL_TEST"] = str(1 << 40)
+        try:
+            t0 = time.perf_counter()
+            cs.cs_batch_ista(b, y, lam, tau, 5, x)
+            st = cs.cs_batch_status_sync(b)
+            secs = time.perf_counter() - t0
+        finally:
+            del os.environ["CS_BATCH_STALL_TEST"]
+        print(f"stalled solve returned {st} after {secs:.2f} s")
+        assert st == cs.CS_ERR_TIMEOUT
+        assert secs < 20.0
+        got = _ista(cs, b, n, ys, lam, tau, [30])
+        for i, inst in enumerate(insts):
+            want = O.ista_fft(inst.c, inst.rows, ys[i].astype(np.float64), lam[i], tau[i], 30)
+            assert rel_l2(got[i], want) <= ITER_TOL
+    finally:
+        b.close()

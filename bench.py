@@ -67,6 +67,9 @@ import synth  # noqa: E402
 
 LAM = 5e-3
 RHO = 1.0
+# 2D deblurring: sigma = rho small against the blur's low-frequency gain, so that
+# ADMM's exact x-update (the inverse of rho H^T H + sigma I) deconvolves
+RHO_2D = 1e-3
 METRIC = "ISTA/ADMM iter/s and time-to-NMSE 1e-4 at n=2^22; fraction of HBM roofline"
 WORKLOAD = "1D ISTA+ADMM, n=2^22, m=n/4, c~N(0,1/m), x* Bernoulli(1/200)-Gaussian, noise 1e-4, lambda=5e-3, rho=1"
 
@@ -831,8 +834,9 @@ def run_deblur2d(args):
     point sources, periodic Gaussian blur sigma = 2.5 px on a 15 x 15
     support, m = n/3 random pixels kept, noise 1e-3): one step = T ISTA + T
     ADMM iterations (tau = 1/||A||^2 by GPU power iteration, lambda = 3
-    sigma_noise ||psf|| sqrt(m/n), rho = 1); pass timings and the roofline of
-    the dominant 2D pass; iterations and time to NMSE 1e-4."""
+    sigma_noise ||psf|| sqrt(m/n), sigma = rho = 1e-3); pass timings and the
+    roofline of the dominant 2D pass; iterations and time to NMSE 1e-2, and
+    the NMSE after 2000 iterations."""
     import torch
     import paper_1707_02244_gb300 as cs
 
@@ -843,6 +847,7 @@ def run_deblur2d(args):
     n, m, T = img.n, img.m, args.iters
     psf = synth.gaussian_psf(2.5)
     lam = float(np.float32(3.0 * 1e-3 * np.linalg.norm(psf) * np.sqrt(m / n)))
+    rho = RHO_2D
     t0 = time.perf_counter()
     plan = cs.cs_plan_2d(img.n0, img.n1, m, img.pix, img.c2, stream)
     plan_ms = 1e3 * (time.perf_counter() - t0)
@@ -858,7 +863,7 @@ def run_deblur2d(args):
     def step():
         x.zero_()
         cs.cs_ista(plan, y, lam, tau, T, x, stats=False)
-        cs.cs_admm(plan, y, lam, RHO, T, z, stats=False)
+        cs.cs_admm(plan, y, lam, rho, T, z, stats=False)
 
     for _ in range(args.warmup):
         step()
@@ -878,14 +883,15 @@ def run_deblur2d(args):
     total_s = sum(ms) / 1e3
     roof, passes = measure_passes(cs, plan, y, x, z, tau, n, m, flush, stream, torch, lam=lam)
     roof["traffic"] = None   # the recorded DRAM figures are for the 1D geometry
-    res = {}
-    cs.cs_set_monitor(plan, xt, 1e-4, 10)
-    xx = torch.zeros(n, dtype=torch.float32, device=dev)
-    st = cs.cs_ista(plan, y, lam, tau, 2000, xx)
-    res["ista"] = {"iters": st["iters_run"], "ms": st["ms"], "nmse": st["nmse"], "reached": bool(st["converged"])}
-    zz = torch.zeros(n, dtype=torch.float32, device=dev)
-    st = cs.cs_admm(plan, y, lam, RHO, 2000, zz)
-    res["admm"] = {"iters": st["iters_run"], "ms": st["ms"], "nmse": st["nmse"], "reached": bool(st["converged"])}
+    res, final = {}, {}
+    for tol, out in ((1e-2, res), (0.0, final)):
+        cs.cs_set_monitor(plan, xt, tol, 10)
+        xx = torch.zeros(n, dtype=torch.float32, device=dev)
+        st = cs.cs_ista(plan, y, lam, tau, 2000, xx)
+        out["ista"] = {"iters": st["iters_run"], "ms": st["ms"], "nmse": st["nmse"], "reached": bool(st["converged"])}
+        zz = torch.zeros(n, dtype=torch.float32, device=dev)
+        st = cs.cs_admm(plan, y, lam, rho, 2000, zz)
+        out["admm"] = {"iters": st["iters_run"], "ms": st["ms"], "nmse": st["nmse"], "reached": bool(st["converged"])}
     cs.cs_set_monitor(plan, None, 0.0, 10)
     line = {
         "metric": "2D compressed deblurring ISTA/ADMM iter/s at 4096x4096; fraction of HBM roofline",
@@ -894,9 +900,11 @@ def run_deblur2d(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "4096x4096 star field, k=20000 log-normal(0,1) fluxes, Gaussian PSF sigma=2.5 px "
                                "(15x15, periodic), m=n/3 random pixels, noise 1e-3",
-                   "n": n, "m": m, "iters_per_solver_per_step": T, "lambda": lam, "tau": tau, "rho": RHO,
+                   "n": n, "m": m, "iters_per_solver_per_step": T, "lambda": lam, "tau": tau, "rho": rho,
+                   "sigma": rho,
                    "l2": "flushed (512 MiB write) between steps, outside the timed events"},
-        "roofline": roof, "passes": passes, "time_to_nmse_1e-4": res, "plan_ms": plan_ms, "clocks": clk,
+        "roofline": roof, "passes": passes, "time_to_nmse_1e-2": res, "after_2000_iters": final,
+        "plan_ms": plan_ms, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     plan.close()

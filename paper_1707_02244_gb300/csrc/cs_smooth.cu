@@ -11,7 +11,9 @@
 //   mid pass:    the twiddle w_n^(j1 k2), length-N1 FFTs along the rows
 //                (j1 -> k1, giving X[k2 + N2 k1] at (k2, k1)), the spectral
 //                operator, and the way back.
-// ISTA transforms its real vectors as complex ones (imaginary part zero);
+// ISTA's vectors are real: a column tile transforms two columns per complex
+// FFT, and the mid pass transforms the rows k2 <= N2/2 of the Hermitian
+// spectra only (whole-CTA instances transform them as complex vectors);
 // ADMM packs (v + mu) + i (z - nu) as in the power-of-two solver and pairs
 // frequency k with n - k: (k2, k1) ~ (N2 - k2, N1 - 1 - k1) for k2 > 0,
 // (0, k1) ~ (0, (N1 - k1) mod N1).
@@ -387,6 +389,82 @@ __device__ void whole_solve(const SmRun& r, const SmInst& d, const SmScal& s, fl
 enum : int { CK_FWD = 0, CK_RES = 1, CK_UPD = 2, CK_ADMM = 3 };
 
 // Column tile u: columns [u G, u G + Gt) of all N2 rows.
+// ISTA column tile u (columns [u G, u G + Gt) of all N2 rows).  Every column
+// is real in the spatial domain, so two columns a, b share one complex
+// transform: forward, Z = FFT(x_a + i x_b) gives A_k = (Z_k + conj Z_{-k}) / 2
+// and B_k = (Z_k - conj Z_{-k}) / 2i; inverse, the spectra of the mid pass
+// are Hermitian along k2 (real results), so IFFT(Y_a + i Y_b) = x_a + i x_b.
+// Gp = ceil(Gt / 2) transforms: column p pairs with p + Gp (when < Gt).  The
+// mid pass reads rows k2 <= N2 / 2 only, so only those are written.
+__device__ void col_tile_ista(const SmRun& r, const SmInst& d, const SmScal& s, int kind, int u, bool last,
+                              float2* A, float2* B, float2* twl) {
+  const int N1 = d.N1, N2 = d.N2, c0 = u * d.G;
+  const int Gt = min(d.G, N1 - c0);
+  const int Gp = (Gt + 1) >> 1;
+  const int tot = Gp * N2;
+  float2* W = r.W + d.woff;
+  twl_load(twl, r.tw + d.twoff + N1, N2);   // read after the barrier below
+  const FDiv dG = fdiv_of(Gp);
+  for (int e = threadIdx.x; e < tot; e += SM_NT) {
+    const int j2 = fdiv(e, dG), pc = e - j2 * Gp;
+    const bool hb = pc + Gp < Gt;
+    const int64_t ga = (int64_t)j2 * N1 + c0 + pc, gb = ga + Gp;
+    float2 v;
+    if (kind == CK_FWD) {
+      v = make_float2(__ldcg(r.x + d.noff + ga), hb ? __ldcg(r.x + d.noff + gb) : 0.f);
+    } else {
+      const float2 ya = __ldcg(W + ga);
+      const float2 yb = hb ? __ldcg(W + gb) : make_float2(0.f, 0.f);
+      v = make_float2(ya.x - yb.y, ya.y + yb.x);   // Y_a + i Y_b
+    }
+    A[pad(e)] = v;
+  }
+  __syncthreads();
+  float2* u2 = A;
+  if (kind != CK_FWD) {
+    u2 = mr_fft<+1>(A, B, N2, Gp, 1, Gp, true, d.r2, d.s2, twl);
+    for (int e = threadIdx.x; e < tot; e += SM_NT) {
+      const int j2 = fdiv(e, dG), pc = e - j2 * Gp;
+      const bool hb = pc + Gp < Gt;
+      const int64_t ta = (int64_t)j2 * N1 + c0 + pc, tb = ta + Gp;
+      const float2 q = u2[pad(e)];
+      float2 o = make_float2(0.f, 0.f);
+      if (kind == CK_RES) {
+        // r~ = M (y~ - C x), both columns
+        const float ya = __ldg(r.yt + d.soff + ta);
+        o.x = isnan(ya) ? 0.f : ya - q.x;
+        if (hb) {
+          const float yb = __ldg(r.yt + d.soff + tb);
+          o.y = isnan(yb) ? 0.f : yb - q.y;
+        }
+      } else {
+        // x <- eta_{tau lambda}(x + tau C^T r~), both columns
+        o.x = soft_s(fmaf(s.tau, q.x, __ldcg(r.x + d.noff + ta)), s.thr);
+        __stcg(r.x + d.noff + ta, o.x);
+        if (hb) {
+          o.y = soft_s(fmaf(s.tau, q.y, __ldcg(r.x + d.noff + tb)), s.thr);
+          __stcg(r.x + d.noff + tb, o.y);
+        }
+      }
+      u2[pad(e)] = o;
+    }
+    __syncthreads();
+    if (last) return;
+  }
+  float2* o = u2 == A ? B : A;
+  u2 = mr_fft<-1>(u2, o, N2, Gp, 1, Gp, true, d.r2, d.s2, twl);
+  const int half = N2 / 2 + 1;          // rows k2 = 0 .. N2 / 2
+  const int hot = Gp * half;
+  for (int e = threadIdx.x; e < hot; e += SM_NT) {
+    const int k2 = fdiv(e, dG), pc = e - k2 * Gp;
+    const int km = k2 == 0 ? 0 : N2 - k2;
+    const float2 z = u2[pad(k2 * Gp + pc)], zm = u2[pad(km * Gp + pc)];
+    const int64_t ga = (int64_t)k2 * N1 + c0 + pc;
+    __stcg(W + ga, make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y)));
+    if (pc + Gp < Gt) __stcg(W + ga + Gp, make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x)));
+  }
+}
+
 __device__ void col_tile(const SmRun& r, const SmInst& d, const SmScal& s, int kind, int u, bool last, float2* A,
                          float2* B, float2* twl) {
   const int N1 = d.N1, N2 = d.N2, c0 = u * d.G;
@@ -432,8 +510,9 @@ __device__ void col_tile(const SmRun& r, const SmInst& d, const SmScal& s, int k
   }
 }
 
-// Mid tile u.  ISTA: rows [u R, u R + nr), op conj(c^) (forward) or c^
-// (adjoint).  ADMM: row 0, row N2/2 (N2 even) or the pair (u, N2 - u).
+// Mid tile u.  ISTA: rows [u R, u R + nr) of k2 <= N2/2, op conj(c^)
+// (forward) or c^ (adjoint), each row also written conjugated at N2 - k2.
+// ADMM: row 0, row N2/2 (N2 even) or the pair (u, N2 - u).
 __device__ void mid_tile(const SmRun& r, const SmInst& d, const SmScal& s, int kind, int u, float2* A, float2* B,
                          float2* twl, float2* tw4) {
   const int N1 = d.N1, N2 = d.N2;
@@ -443,9 +522,11 @@ __device__ void mid_tile(const SmRun& r, const SmInst& d, const SmScal& s, int k
     k2b = N2 - u;
     nr = (u == 0 || 2 * u == N2) ? 1 : 2;
   } else {
+    // ISTA: the spectra are Hermitian along k2 (real vectors), so only rows
+    // k2 <= N2 / 2 are transformed; row N2 - k2 is written as the conjugate
     k2a = u * d.R;
     k2b = 0;
-    nr = min(d.R, N2 - k2a);
+    nr = min(d.R, N2 / 2 + 1 - k2a);
   }
   float2* W = r.W + d.woff;
   const float2* tw1 = r.tw + d.twoff;
@@ -501,7 +582,9 @@ __device__ void mid_tile(const SmRun& r, const SmInst& d, const SmScal& s, int k
   for (int e = threadIdx.x; e < tot; e += SM_NT) {
     const int f = fdiv(e, dN1), j1 = e - f * N1;
     const int k2 = row_of(f);
-    __stcg(W + (int64_t)k2 * N1 + j1, cscale(cmulc(u2[pad(e)], fourstep(j1, k2)), d.inv_n));
+    const float2 v = cscale(cmulc(u2[pad(e)], fourstep(j1, k2)), d.inv_n);
+    __stcg(W + (int64_t)k2 * N1 + j1, v);
+    if (kind != 2 && k2 != 0 && 2 * k2 != N2) __stcg(W + (int64_t)(N2 - k2) * N1 + j1, cconj(v));
   }
 }
 
@@ -620,7 +703,8 @@ __global__ void __launch_bounds__(SM_NT, 3) smooth_solve_k(const SmRun r) {
     __syncthreads();
     if (!s_ok) return;
     const SmScal s = r.sc[j];
-    if (col) col_tile(r, sd, s, kind, u, last, A, B, s_twl);
+    if (col && kind != CK_ADMM) col_tile_ista(r, sd, s, kind, u, last, A, B, s_twl);
+    else if (col) col_tile(r, sd, s, kind, u, last, A, B, s_twl);
     else mid_tile(r, sd, s, kind, u, A, B, s_twl, s_tw4);
     __syncthreads();   // every store of the tile issued
     if (threadIdx.x == 0) {
@@ -791,7 +875,7 @@ void fill_geometry(SmInst& d, int64_t n, const Split* sp) {
   d.nmid = 0;   // per solver: set by tiles_for
 }
 
-int mid_tiles(const SmInst& d, bool admm) { return admm ? d.N2 / 2 + 1 : (d.N2 + d.R - 1) / d.R; }
+int mid_tiles(const SmInst& d, bool admm) { return admm ? d.N2 / 2 + 1 : (d.N2 / 2 + d.R) / d.R; }
 
 cudaError_t set_smem_attr() {
   static cudaError_t e = cudaFuncSetAttribute(smooth_solve_k, cudaFuncAttributeMaxDynamicSharedMemorySize,

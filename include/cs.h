@@ -236,7 +236,10 @@ cs_status cs_grad_admm(cs_plan_t plan, const float* y, float lambda, const cs_ad
  *     instances are solved by ONE persistent launch per call whose CTAs take
  *     (instance, pass, tile) items from a device-side queue; a tile waits,
  *     bounded, for its instance's previous pass (CS_ERR_TIMEOUT from
- *     cs_batch_status_sync if a wait ran out).
+ *     cs_batch_status_sync if a wait ran out: each wait gives up after 2 s,
+ *     every CTA then stops and the launch returns).  For tests only, the
+ *     environment variable CS_BATCH_STALL_TEST=k raises every count the
+ *     first such instance waits for by k, so that a wait runs out.
  * The concatenated vectors may hold instances of odd length: any 4-byte
  * offset is accepted.
  * --------------------------------------------------------------------- */

@@ -231,8 +231,10 @@ cs_status cs_grad_admm(cs_plan_t plan, const float* y, float lambda, const cs_ad
  *   - 7-smooth n_i = 2^a 3^b 5^c 7^d that is not a power of two: mixed-radix
  *     FFTs (radices 8, 4, 2, 7, 5, 3), one CTA per instance up to n_i = 4096,
  *     above it a four-step split n_i = N1 N2 chosen by a plan-time tuner
- *     (cached per n for the process; the environment variable
- *     CS_BATCH_AUTOTUNE=0 keeps the heuristic split).  All of these
+ *     (cached per n for the process; CS_BATCH_AUTOTUNE=0 in the
+ *     environment keeps the heuristic split; CS_BATCH_TUNE_CACHE=<file>
+ *     keeps the tuned splits across processes as JSON keyed by the GPU's
+ *     name, read once per process and rewritten after each new tuning).  All of these
  *     instances are solved by ONE persistent launch per call whose CTAs take
  *     (instance, pass, tile) items from a device-side queue; a tile waits,
  *     bounded, for its instance's previous pass (CS_ERR_TIMEOUT from

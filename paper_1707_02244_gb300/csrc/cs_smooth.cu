@@ -35,10 +35,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/cs.h"
@@ -948,6 +951,79 @@ cudaError_t salloc(T** p, size_t count) {
 std::mutex g_tune_mu;
 std::map<int64_t, Split> g_tuned;
 
+// Tuner cache file (opt-in).  With CS_BATCH_TUNE_CACHE=<path>, the tuned
+// splits persist across processes as JSON keyed by the GPU's name:
+//   {"device": "<name>", "splits": {"<n>": [N1, N2, G], ...}}
+// The file is read once per process (before the first tuning) and rewritten,
+// through a temporary file and a rename, after every newly tuned n.  A file
+// for another GPU is ignored, and so is any entry that is not one of the
+// feasible splits of its n (split_candidates), so a stale or edited file can
+// never give an invalid geometry.
+bool g_tune_file_read = false;
+
+std::string tune_device_name() {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "";
+  return prop.name;
+}
+
+bool feasible_split(int64_t n, const Split& sp) {
+  for (const Split& c : split_candidates(n))
+    if (c.N1 == sp.N1 && c.N2 == sp.N2 && c.G == sp.G) return true;
+  return false;
+}
+
+// Caller holds g_tune_mu.
+void read_tune_file(const char* path) {
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return;
+  std::string txt;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, got);
+  std::fclose(f);
+  const size_t kd = txt.find("\"device\"");
+  if (kd == std::string::npos) return;
+  const size_t q0 = txt.find('"', txt.find(':', kd));
+  const size_t q1 = q0 == std::string::npos ? q0 : txt.find('"', q0 + 1);
+  if (q1 == std::string::npos || txt.substr(q0 + 1, q1 - q0 - 1) != tune_device_name()) return;
+  size_t pos = txt.find("\"splits\"");
+  if (pos == std::string::npos) return;
+  pos = txt.find('{', pos);
+  while (pos != std::string::npos) {
+    const size_t a = txt.find('"', pos);
+    if (a == std::string::npos) break;
+    long long n = 0;
+    int N1 = 0, N2 = 0, G = 0;
+    if (std::sscanf(txt.c_str() + a, "\"%lld\" : [ %d , %d , %d ]", &n, &N1, &N2, &G) == 4 ||
+        std::sscanf(txt.c_str() + a, "\"%lld\": [%d, %d, %d]", &n, &N1, &N2, &G) == 4) {
+      const Split sp{N1, N2, G};
+      if (n > 0 && feasible_split(n, sp)) g_tuned.emplace((int64_t)n, sp);
+    }
+    pos = txt.find(']', a);
+  }
+}
+
+// Caller holds g_tune_mu.
+void write_tune_file(const char* path) {
+  std::string txt = "{\"device\": \"" + tune_device_name() + "\",\n \"splits\": {";
+  bool first = true;
+  for (const auto& kv : g_tuned) {
+    char line[96];
+    std::snprintf(line, sizeof line, "%s\n  \"%lld\": [%d, %d, %d]", first ? "" : ",", (long long)kv.first,
+                  kv.second.N1, kv.second.N2, kv.second.G);
+    txt += line;
+    first = false;
+  }
+  txt += "\n }}\n";
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return;
+  const bool ok = std::fwrite(txt.data(), 1, txt.size(), f) == txt.size();
+  if (std::fclose(f) != 0 || !ok || std::rename(tmp.c_str(), path) != 0) std::remove(tmp.c_str());
+}
+
 cudaError_t tune_split(int64_t n, cudaStream_t s, Split* out) {
   const std::vector<Split> cand = split_candidates(n);
   if (cand.empty()) return cudaErrorInvalidValue;
@@ -956,8 +1032,14 @@ cudaError_t tune_split(int64_t n, cudaStream_t s, Split* out) {
     *out = cand[0];
     return cudaSuccess;
   }
+  const char* cache = std::getenv("CS_BATCH_TUNE_CACHE");
+  if (cache && !cache[0]) cache = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (cache && !g_tune_file_read) {
+      read_tune_file(cache);
+      g_tune_file_read = true;
+    }
     auto it = g_tuned.find(n);
     if (it != g_tuned.end()) {
       *out = it->second;
@@ -1063,6 +1145,7 @@ cudaError_t tune_split(int64_t n, cudaStream_t s, Split* out) {
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tuned[n] = best;
+  if (cache) write_tune_file(cache);
   *out = best;
   return cudaSuccess;
 }

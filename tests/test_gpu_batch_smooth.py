@@ -216,3 +216,39 @@ def test_smooth_batch_bounded_wait_times_out(cs):
             assert rel_l2(got[i], want) <= ITER_TOL
     finally:
         b.close()
+
+
+def test_tuner_cache_file_round_trip(tmp_path):
+    """With CS_BATCH_TUNE_CACHE set, the plan-time tuner keeps its chosen
+    splits in a JSON file keyed by the GPU's name.  A first process tunes two
+    four-step sizes and writes them; a second process reads the file and
+    tunes nothing (the file is not rewritten).  Each process starts with an
+    empty in-memory cache, so the file is what the second one uses."""
+    import json
+    import pathlib
+    import subprocess
+    import sys
+    root = str(pathlib.Path(__file__).resolve().parents[1])
+    path = tmp_path / "tune.json"
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import numpy as np, torch\n"
+        "import paper_1707_02244_gb300 as cs, synth\n"
+        "n = np.array([6615, 10080], dtype=np.int64); m = n // 4\n"
+        "insts = synth.batch_instances(n, m)\n"
+        "b = cs.cs_batch_plan(n, m, np.concatenate([i.rows for i in insts]),\n"
+        "                     np.concatenate([i.c for i in insts]), torch.cuda.current_stream())\n"
+        "b.close()\n"
+        "print(torch.cuda.get_device_name(0))\n" % root)
+    env = dict(os.environ, CS_BATCH_TUNE_CACHE=str(path))
+    env.pop("CS_BATCH_AUTOTUNE", None)
+    first = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, check=True,
+                           capture_output=True, text=True)
+    data = json.loads(path.read_text())
+    assert data["device"] == first.stdout.strip().splitlines()[-1]
+    assert set(data["splits"]) == {"6615", "10080"}
+    for key, (n1, n2, g) in data["splits"].items():
+        assert n1 * n2 == int(key) and 1 <= g <= 8
+    stamp = path.stat().st_mtime_ns
+    subprocess.run([sys.executable, "-c", code], env=env, cwd=root, check=True, capture_output=True)
+    assert path.stat().st_mtime_ns == stamp

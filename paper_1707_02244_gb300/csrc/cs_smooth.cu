@@ -621,98 +621,160 @@ __device__ bool wait_count(const unsigned long long* cnt, unsigned long long nee
   return false;
 }
 
+// A phase item decoded: instance j, pass kind, column or mid tile u, whether
+// it is the solve's last column pass, and the completed-tile count of
+// instance j it must wait for.
+struct SmItem {
+  int j, kind, col, u;
+  bool last;
+  unsigned long long need;
+};
+
+__device__ SmItem decode_item(const SmRun& r, long long item) {
+  const long long C = r.C, M = r.M;
+  long long p = item - r.n_whole;
+  SmItem it;
+  it.last = false;
+  if (!r.admm) {
+    if (p < C) {
+      it.col = 1;
+      it.kind = CK_FWD;
+      const int2 m = r.cmap[p];
+      it.j = m.x;
+      it.u = m.y;
+      it.need = 0;
+    } else {
+      p -= C;
+      const long long per = 2 * C + 2 * M;
+      const long long t = p / per;
+      long long q = p - t * per;
+      int ph;
+      if (q < M) ph = 0;
+      else if (q < M + C) { ph = 1; q -= M; }
+      else if (q < 2 * M + C) { ph = 2; q -= M + C; }
+      else { ph = 3; q -= 2 * M + C; }
+      it.col = ph & 1;
+      const int2 m = it.col ? r.cmap[q] : r.mmap[q];
+      it.j = m.x;
+      it.u = m.y;
+      it.kind = ph == 0 ? 0 : (ph == 1 ? CK_RES : (ph == 2 ? 1 : CK_UPD));
+      it.last = ph == 3 && t + 1 == r.iters;
+      const SmInst& di = r.inst[it.j];
+      const unsigned long long nc = (unsigned)di.ncol, nm = (unsigned)di.nmid;
+      const unsigned long long off = ph == 0 ? 0 : (ph == 1 ? nm : (ph == 2 ? nm + nc : 2 * nm + nc));
+      it.need = nc + (unsigned long long)t * (2 * nc + 2 * nm) + off;
+    }
+  } else {
+    const long long per = C + M;
+    const long long t = p / per;
+    long long q = p - t * per;
+    it.col = q >= M;
+    if (it.col) q -= M;
+    const int2 m = it.col ? r.cmap[q] : r.mmap[q];
+    it.j = m.x;
+    it.u = m.y;
+    it.kind = it.col ? CK_ADMM : 2;
+    it.last = it.col && t + 1 == r.iters;
+    const SmInst& di = r.inst[it.j];
+    const unsigned long long nc = (unsigned)di.ncol, nm = (unsigned)di.nmid;
+    it.need = (unsigned long long)t * (nc + nm) + (it.col ? nm : 0);
+  }
+  if (r.stall != 0ull && it.j == 0) it.need += r.stall;   // a count that is never reached
+  return it;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* a) { asm volatile("prefetch.global.L2 [%0];" ::"l"(a)); }
+
+// Bring the inputs of a phase item into L2 (every thread issues a share of
+// the 128-byte lines).  Only a hint: the data may still change before the
+// item runs (L2 is coherent), and nothing waits for it.
+__device__ void prefetch_item(const SmRun& r, const SmItem& it) {
+  const SmInst& d = r.inst[it.j];
+  const int N1 = d.N1, N2 = d.N2;
+  const float2* W = r.W + d.woff;
+  if (it.col) {
+    // one line per row of each strided column block (<= 8 columns)
+    const int c0 = it.u * d.G;
+    for (int j2 = threadIdx.x; j2 < N2; j2 += SM_NT) {
+      const int64_t g = (int64_t)j2 * N1 + c0;
+      if (it.kind != CK_FWD) prefetch_l2(W + g);
+      if (it.kind == CK_FWD || it.kind == CK_UPD) prefetch_l2(r.x + d.noff + g);
+      if (it.kind == CK_RES || it.kind == CK_ADMM) prefetch_l2(r.yt + d.soff + g);
+      if (it.kind == CK_ADMM) {
+        prefetch_l2(r.mu + d.soff + g);
+        prefetch_l2(r.nu + d.soff + g);
+      }
+    }
+  } else {
+    // whole rows: the exchange rows and the spectrum rows
+    int ka, nr;
+    if (it.kind == 2) { ka = it.u; nr = 1; }
+    else { ka = it.u * d.R; nr = min(d.R, N2 / 2 + 1 - ka); }
+    for (int f = 0; f < (it.kind == 2 && it.u != 0 && 2 * it.u != N2 ? 2 : nr); ++f) {
+      const int k2 = it.kind == 2 ? (f == 0 ? ka : N2 - ka) : ka + f;
+      const float2* wr = W + (int64_t)k2 * N1;
+      const float2* cr = r.chat + d.soff + (int64_t)k2 * N1;
+      for (int q = 16 * threadIdx.x; q < N1; q += 16 * SM_NT) {
+        prefetch_l2(wr + q);
+        prefetch_l2(cr + q);
+      }
+    }
+  }
+}
+
+// Take the next item number from the queue (-1 once a wait has timed out).
+__device__ __forceinline__ long long take_item(const SmRun& r) {
+  return (ld_status(r.status) & STS_TIMEOUT) ? -1 : (long long)atomicAdd(r.queue, 1ull);
+}
+
 __global__ void __launch_bounds__(SM_NT, 3) smooth_solve_k(const SmRun r) {
   extern __shared__ float2 sbuf[];
   __shared__ SmInst sd;
   __shared__ float2 s_twl[TWL_LO + TWL_HI];
   __shared__ float2 s_tw4[2 * (TWL_LO + TWL_HI)];
-  __shared__ long long s_item;
+  __shared__ long long s_item, s_next;
   __shared__ int s_ok;
   float2* A = sbuf;
   float2* B = sbuf + smem_slots(SM_TILE);
-  const long long C = r.C, M = r.M;
+  // A CTA claims its next item when it starts the current one and prefetches
+  // that item's inputs into L2 meanwhile.  Items are still claimed in queue
+  // order, and an item only ever waits on smaller item numbers, so the
+  // smallest unfinished item always runs: the schedule cannot deadlock.
+  if (threadIdx.x == 0) s_item = take_item(r);
   for (;;) {
-    if (threadIdx.x == 0) {
-      long long it = -1;
-      if (!(ld_status(r.status) & STS_TIMEOUT)) it = (long long)atomicAdd(r.queue, 1ull);
-      s_item = it;
-    }
     __syncthreads();
     const long long item = s_item;
     if (item < 0 || item >= r.items) return;
+    if (threadIdx.x == 0) s_next = take_item(r);
+    __syncthreads();
+    const long long nxt = s_next;
+    if (nxt >= r.n_whole && nxt < r.items) prefetch_item(r, decode_item(r, nxt));
     if (item < r.n_whole) {
       const int j = r.whole[item];
       if (threadIdx.x == 0) sd = r.inst[j];
       __syncthreads();
       whole_solve(r, sd, r.sc[j], A, B, s_twl);
       __syncthreads();
+      if (threadIdx.x == 0) s_item = nxt;
       continue;
     }
-    // phase item: decode (pass kind, iteration, tile) and the counter it needs
-    long long p = item - r.n_whole;
-    int kind, col, u, j;
-    bool last = false;
-    unsigned long long need;
-    if (!r.admm) {
-      if (p < C) {
-        col = 1;
-        kind = CK_FWD;
-        const int2 m = r.cmap[p];
-        j = m.x;
-        u = m.y;
-        need = 0;
-      } else {
-        p -= C;
-        const long long per = 2 * C + 2 * M;
-        const long long t = p / per;
-        long long q = p - t * per;
-        int ph;
-        if (q < M) ph = 0;
-        else if (q < M + C) { ph = 1; q -= M; }
-        else if (q < 2 * M + C) { ph = 2; q -= M + C; }
-        else { ph = 3; q -= 2 * M + C; }
-        col = ph & 1;
-        const int2 m = col ? r.cmap[q] : r.mmap[q];
-        j = m.x;
-        u = m.y;
-        kind = ph == 0 ? 0 : (ph == 1 ? CK_RES : (ph == 2 ? 1 : CK_UPD));
-        last = ph == 3 && t + 1 == r.iters;
-        const SmInst& di = r.inst[j];
-        const unsigned long long nc = (unsigned)di.ncol, nm = (unsigned)di.nmid;
-        const unsigned long long off = ph == 0 ? 0 : (ph == 1 ? nm : (ph == 2 ? nm + nc : 2 * nm + nc));
-        need = nc + (unsigned long long)t * (2 * nc + 2 * nm) + off;
-      }
-    } else {
-      const long long per = C + M;
-      const long long t = p / per;
-      long long q = p - t * per;
-      col = q >= M;
-      if (col) q -= M;
-      const int2 m = col ? r.cmap[q] : r.mmap[q];
-      j = m.x;
-      u = m.y;
-      kind = col ? CK_ADMM : 2;
-      last = col && t + 1 == r.iters;
-      const SmInst& di = r.inst[j];
-      const unsigned long long nc = (unsigned)di.ncol, nm = (unsigned)di.nmid;
-      need = (unsigned long long)t * (nc + nm) + (col ? nm : 0);
-    }
-    if (r.stall != 0ull && j == 0) need += r.stall;   // a count that is never reached
+    const SmItem it = decode_item(r, item);
     if (threadIdx.x == 0) {
-      sd = r.inst[j];
-      s_ok = wait_count(r.done + j, need, r.status);
+      sd = r.inst[it.j];
+      s_ok = wait_count(r.done + it.j, it.need, r.status);
       __threadfence();
     }
     __syncthreads();
     if (!s_ok) return;
-    const SmScal s = r.sc[j];
-    if (col && kind != CK_ADMM) col_tile_ista(r, sd, s, kind, u, last, A, B, s_twl);
-    else if (col) col_tile(r, sd, s, kind, u, last, A, B, s_twl);
-    else mid_tile(r, sd, s, kind, u, A, B, s_twl, s_tw4);
+    const SmScal s = r.sc[it.j];
+    if (it.col && it.kind != CK_ADMM) col_tile_ista(r, sd, s, it.kind, it.u, it.last, A, B, s_twl);
+    else if (it.col) col_tile(r, sd, s, it.kind, it.u, it.last, A, B, s_twl);
+    else mid_tile(r, sd, s, it.kind, it.u, A, B, s_twl, s_tw4);
     __syncthreads();   // every store of the tile issued
     if (threadIdx.x == 0) {
       __threadfence();
-      atomicAdd(r.done + j, 1ull);
+      atomicAdd(r.done + it.j, 1ull);
+      s_item = nxt;
     }
   }
 }

@@ -96,6 +96,7 @@ struct SmRun {
   unsigned long long* done;    // per instance: tiles completed
   int* status;
   unsigned long long stall;    // test hook: added to every count instance 0 waits for (0: off)
+  int lookahead;               // claim the next item early and prefetch it (set by launch_solve)
 };
 
 namespace {
@@ -736,16 +737,19 @@ __global__ void __launch_bounds__(SM_NT, 3) smooth_solve_k(const SmRun r) {
   __shared__ int s_ok;
   float2* A = sbuf;
   float2* B = sbuf + smem_slots(SM_TILE);
-  // A CTA claims its next item when it starts the current one and prefetches
+  // With look-ahead (every pass has many more tiles than there are CTAs), a
+  // CTA claims its next item when it starts the current one and prefetches
   // that item's inputs into L2 meanwhile.  Items are still claimed in queue
   // order, and an item only ever waits on smaller item numbers, so the
   // smallest unfinished item always runs: the schedule cannot deadlock.
+  // Without it (few tiles per pass) an early claim would take a tile away
+  // from an idle CTA, so the next item is claimed only after the current.
   if (threadIdx.x == 0) s_item = take_item(r);
   for (;;) {
     __syncthreads();
     const long long item = s_item;
     if (item < 0 || item >= r.items) return;
-    if (threadIdx.x == 0) s_next = take_item(r);
+    if (threadIdx.x == 0) s_next = r.lookahead ? take_item(r) : -2;
     __syncthreads();
     const long long nxt = s_next;
     if (nxt >= r.n_whole && nxt < r.items) prefetch_item(r, decode_item(r, nxt));
@@ -755,7 +759,7 @@ __global__ void __launch_bounds__(SM_NT, 3) smooth_solve_k(const SmRun r) {
       __syncthreads();
       whole_solve(r, sd, r.sc[j], A, B, s_twl);
       __syncthreads();
-      if (threadIdx.x == 0) s_item = nxt;
+      if (threadIdx.x == 0) s_item = r.lookahead ? nxt : take_item(r);
       continue;
     }
     const SmItem it = decode_item(r, item);
@@ -774,7 +778,7 @@ __global__ void __launch_bounds__(SM_NT, 3) smooth_solve_k(const SmRun r) {
     if (threadIdx.x == 0) {
       __threadfence();
       atomicAdd(r.done + it.j, 1ull);
-      s_item = nxt;
+      s_item = r.lookahead ? nxt : take_item(r);
     }
   }
 }
@@ -958,6 +962,8 @@ cudaError_t launch_solve(const SmRun& r, cudaStream_t s) {
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, smooth_solve_k, SM_NT, smem)) != cudaSuccess) return e;
   const long long grid = std::min<long long>(r.items, (long long)std::max(1, per) * sms);
+  SmRun rr = r;
+  rr.lookahead = (r.C > 0 && r.M > 0 && std::min(r.C, r.M) >= 2 * grid) ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(SM_NT);
@@ -968,7 +974,7 @@ cudaError_t launch_solve(const SmRun& r, cudaStream_t s) {
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, smooth_solve_k, r);
+  return cudaLaunchKernelEx(&cfg, smooth_solve_k, rr);
 }
 
 }  // namespace

@@ -190,28 +190,30 @@ def cs_opnorm2(plan: Plan, iters: int = 100) -> float:
 
 
 def cs_forward(plan: Plan, x, y):
-    _check(_lib.cs_forward(plan.handle, _ptr(x), _ptr(y)), "cs_forward")
+    _check(_lib.cs_forward(plan.handle, _ptr(x, numel=plan.n), _ptr(y, numel=plan.m)), "cs_forward")
 
 
 def cs_adjoint(plan: Plan, r, x):
-    _check(_lib.cs_adjoint(plan.handle, _ptr(r), _ptr(x)), "cs_adjoint")
+    _check(_lib.cs_adjoint(plan.handle, _ptr(r, numel=plan.m), _ptr(x, numel=plan.n)), "cs_adjoint")
 
 
 def cs_set_monitor(plan: Plan, x_true=None, nmse_tol: float = 0.0, check_every: int = 10):
-    _check(_lib.cs_set_monitor(plan.handle, _ptr(x_true), float(nmse_tol), int(check_every)),
+    _check(_lib.cs_set_monitor(plan.handle, _ptr(x_true, numel=plan.n), float(nmse_tol), int(check_every)),
            "cs_set_monitor")
 
 
 def cs_ista(plan: Plan, y, lam: float, tau: float, iters: int, x, stats: bool = True):
     st = CsStats()
-    code = _lib.cs_ista(plan.handle, _ptr(y), lam, tau, iters, _ptr(x), ctypes.byref(st) if stats else None)
+    code = _lib.cs_ista(plan.handle, _ptr(y, numel=plan.m), lam, tau, iters, _ptr(x, numel=plan.n),
+                        ctypes.byref(st) if stats else None)
     _check(code, "cs_ista")
     return st.as_dict() if stats else None
 
 
 def cs_admm(plan: Plan, y, lam: float, rho: float, iters: int, z, stats: bool = True):
     st = CsStats()
-    code = _lib.cs_admm(plan.handle, _ptr(y), lam, rho, iters, _ptr(z), ctypes.byref(st) if stats else None)
+    code = _lib.cs_admm(plan.handle, _ptr(y, numel=plan.m), lam, rho, iters, _ptr(z, numel=plan.n),
+                        ctypes.byref(st) if stats else None)
     _check(code, "cs_admm")
     return st.as_dict() if stats else None
 
@@ -220,8 +222,10 @@ def cs_admm_ex(plan: Plan, y, lam: float, sigma: float, rho: float, tau1: float,
                iters: int, warm: bool, x, z, mu, nu, v, stats: bool = True):
     st = CsStats()
     prm = CsAdmmParams(sigma, rho, tau1, tau2)
-    code = _lib.cs_admm_ex(plan.handle, _ptr(y), lam, ctypes.byref(prm), iters, int(bool(warm)),
-                           _ptr(x), _ptr(z), _ptr(mu), _ptr(nu), _ptr(v),
+    n = plan.n
+    code = _lib.cs_admm_ex(plan.handle, _ptr(y, numel=plan.m), lam, ctypes.byref(prm), iters, int(bool(warm)),
+                           _ptr(x, numel=n), _ptr(z, numel=n), _ptr(mu, numel=n), _ptr(nu, numel=n),
+                           _ptr(v, numel=n),
                            ctypes.byref(st) if stats else None)
     _check(code, "cs_admm_ex")
     return st.as_dict() if stats else None
@@ -230,8 +234,9 @@ def cs_admm_ex(plan: Plan, y, lam: float, sigma: float, rho: float, tau1: float,
 def cs_grad(plan: Plan, y, lam: float, tau: float, T: int, K: int, gx_T, dc, dlam, dy):
     """Reverse mode of T ISTA steps from x(0) = 0: dc, dlam (1 element) and
     dy receive dL/dc, dL/dlambda, dL/dy for gx_T = dL/dx(T)."""
-    _check(_lib.cs_grad(plan.handle, _ptr(y), lam, tau, int(T), int(K), _ptr(gx_T), _ptr(dc), _ptr(dlam),
-                        _ptr(dy)), "cs_grad")
+    n, m = plan.n, plan.m
+    _check(_lib.cs_grad(plan.handle, _ptr(y, numel=m), lam, tau, int(T), int(K), _ptr(gx_T, numel=n),
+                        _ptr(dc, numel=n), _ptr(dlam, numel=1), _ptr(dy, numel=m)), "cs_grad")
 
 
 def cs_grad_admm(plan: Plan, y, lam: float, sigma: float, rho: float, tau1: float, tau2: float, T: int, K: int,
@@ -240,8 +245,10 @@ def cs_grad_admm(plan: Plan, y, lam: float, sigma: float, rho: float, tau1: floa
     dlam (1 element) and dy receive dL/dc, dL/dlambda, dL/dy for gz_T =
     dL/dz(T) (and gx_T = dL/dx(T) when the loss also depends on x(T))."""
     prm = CsAdmmParams(sigma, rho, tau1, tau2)
-    _check(_lib.cs_grad_admm(plan.handle, _ptr(y), lam, ctypes.byref(prm), int(T), int(K), _ptr(gz_T),
-                             _ptr(gx_T), _ptr(dc), _ptr(dlam), _ptr(dy)), "cs_grad_admm")
+    n, m = plan.n, plan.m
+    _check(_lib.cs_grad_admm(plan.handle, _ptr(y, numel=m), lam, ctypes.byref(prm), int(T), int(K),
+                             _ptr(gz_T, numel=n), _ptr(gx_T, numel=n), _ptr(dc, numel=n), _ptr(dlam, numel=1),
+                             _ptr(dy, numel=m)), "cs_grad_admm")
 
 
 def _make_unrolled_ista():
@@ -297,8 +304,9 @@ def __getattr__(name):
 def cs_forward_direct(n: int, m: int, c, rows, x, y, stream=None):
     """y = A x by one O(n) dot product per kept row (context comparator);
     c float32 device (n,), rows int32 device (m,)."""
-    rptr = int(rows.data_ptr()) if hasattr(rows, "data_ptr") else int(rows)
-    _check(_lib.cs_forward_direct(int(n), int(m), _ptr(c), rptr, _ptr(x), _ptr(y), _stream_handle(stream)),
+    rptr = _ptr(rows, dtype="torch.int32", numel=int(m))
+    _check(_lib.cs_forward_direct(int(n), int(m), _ptr(c, numel=int(n)), rptr, _ptr(x, numel=int(n)),
+                                  _ptr(y, numel=int(m)), _stream_handle(stream)),
            "cs_forward_direct")
 
 
@@ -369,14 +377,16 @@ def _host_f32(v, count: int) -> np.ndarray:
 def cs_batch_ista(batch: BatchPlan, y, lam, tau, iters: int, x):
     """lam, tau: scalars or per-instance sequences (host)."""
     lam_h, tau_h = _host_f32(lam, batch.count), _host_f32(tau, batch.count)
-    _check(_lib.cs_batch_ista(batch.handle, _ptr(y), lam_h.ctypes.data, tau_h.ctypes.data, int(iters), _ptr(x)),
-           "cs_batch_ista")
+    sn, sm = int(batch.n.sum()), int(batch.m.sum())
+    _check(_lib.cs_batch_ista(batch.handle, _ptr(y, numel=sm), lam_h.ctypes.data, tau_h.ctypes.data, int(iters),
+                              _ptr(x, numel=sn)), "cs_batch_ista")
 
 
 def cs_batch_admm(batch: BatchPlan, y, lam, rho, iters: int, z):
     lam_h, rho_h = _host_f32(lam, batch.count), _host_f32(rho, batch.count)
-    _check(_lib.cs_batch_admm(batch.handle, _ptr(y), lam_h.ctypes.data, rho_h.ctypes.data, int(iters), _ptr(z)),
-           "cs_batch_admm")
+    sn, sm = int(batch.n.sum()), int(batch.m.sum())
+    _check(_lib.cs_batch_admm(batch.handle, _ptr(y, numel=sm), lam_h.ctypes.data, rho_h.ctypes.data, int(iters),
+                              _ptr(z, numel=sn)), "cs_batch_admm")
 
 
 def cs_batch_status_sync(batch: BatchPlan) -> int:

@@ -176,3 +176,61 @@ def test_ptr_checks_length(cs):
         cs._ptr(torch.zeros(4, dtype=torch.float32), numel=8)
     with pytest.raises(TypeError):
         cs._ptr(torch.zeros(4, dtype=torch.float64))
+
+
+class _FakeDeviceTensor:
+    """Looks like a contiguous float32 CUDA tensor of `k` elements; the
+    binding checks it without touching a device (its address is never used,
+    because every call below fails the length check first)."""
+
+    def __init__(self, k, dtype="torch.float32"):
+        self.k, self.dtype = k, dtype
+
+    def data_ptr(self):
+        return 1 << 20
+
+    def is_contiguous(self):
+        return True
+
+    is_cuda = True
+
+    def numel(self):
+        return self.k
+
+
+def test_binding_rejects_short_vectors_before_any_call(cs):
+    """Every binding call that takes device vectors checks their lengths
+    against the plan (n-vectors, m-vectors, the batch's concatenations)
+    before the library is called: a short tensor would otherwise make the
+    kernels read or write past its end."""
+    n, m = 64, 16
+    plan = cs.Plan(None, n, m)          # no library handle: nothing may reach the library
+    good_n, good_m = _FakeDeviceTensor(n), _FakeDeviceTensor(m)
+    short_n, short_m = _FakeDeviceTensor(n - 1), _FakeDeviceTensor(m - 1)
+    calls = [
+        lambda: cs.cs_forward(plan, short_n, good_m),
+        lambda: cs.cs_forward(plan, good_n, short_m),
+        lambda: cs.cs_adjoint(plan, short_m, good_n),
+        lambda: cs.cs_adjoint(plan, good_m, short_n),
+        lambda: cs.cs_set_monitor(plan, short_n, 1e-4, 10),
+        lambda: cs.cs_ista(plan, short_m, 1e-3, 0.1, 1, good_n),
+        lambda: cs.cs_ista(plan, good_m, 1e-3, 0.1, 1, short_n),
+        lambda: cs.cs_admm(plan, good_m, 1e-3, 1.0, 1, short_n),
+        lambda: cs.cs_admm_ex(plan, good_m, 1e-3, 1.0, 1.0, 1.0, 1.0, 1, False, None, good_n, good_n,
+                              short_n, good_n),
+        lambda: cs.cs_grad(plan, good_m, 1e-3, 0.1, 4, 2, good_n, good_n, _FakeDeviceTensor(0), good_m),
+        lambda: cs.cs_grad(plan, good_m, 1e-3, 0.1, 4, 2, good_n, short_n, _FakeDeviceTensor(1), good_m),
+        lambda: cs.cs_forward_direct(n, m, short_n, _FakeDeviceTensor(m, "torch.int32"), good_n, good_m),
+        lambda: cs.cs_forward_direct(n, m, good_n, _FakeDeviceTensor(m - 1, "torch.int32"), good_n, good_m),
+    ]
+    batch = cs.BatchPlan(None, [32, 32], [8, 8])
+    calls += [
+        lambda: cs.cs_batch_ista(batch, _FakeDeviceTensor(15), 1e-3, 0.1, 1, _FakeDeviceTensor(64)),
+        lambda: cs.cs_batch_admm(batch, _FakeDeviceTensor(16), 1e-3, 1.0, 1, _FakeDeviceTensor(63)),
+    ]
+    for k, call in enumerate(calls):
+        with pytest.raises(ValueError, match="expected at least"):
+            call()
+    # an int32 row list is required by the direct product
+    with pytest.raises(TypeError):
+        cs.cs_forward_direct(n, m, good_n, _FakeDeviceTensor(m), good_n, good_m)
